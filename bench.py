@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: output audio samples/s of batched nonlinear string synthesis.
+
+Workload (one "step"): 256 strings, 2 s at 48 kHz each (96,000 samples),
+f0 log-uniform 40-1000 Hz, kappa U[0.5,3], alpha U[1,10], sigma0 U[0.1,2],
+sigma1 U[1e-6,1e-4], excitation uniform over pluck / hammer / bow (seed 2),
+synthesized from the initial state by one launch of the persistent step
+kernel.  Every step starts from freshly created strings (inputs resident in
+device memory before the timed region); L2 is flushed between timed steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank synthesizes its own 256-string batch (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle (the only reference this
+method has) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2311_18505_gb300 import workloads as W  # noqa: E402
+
+METRIC = "output audio samples/s (all strings)"
+UNIT = "samples/s"
+FS = 48000.0
+SM_COUNT_GB300 = 152
+# FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz max SM clock
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+# Algorithmic FLOPs per grid-point update (one exact step, no repeated
+# sweeps): stencil right-hand side, matrix assembly, one exact tridiagonal
+# factor + solve and the coupling terms; see the design notes for the count.
+FLOP_U_LINEAR = 24.0      # RHS 19 + prefactored solve 5
+FLOP_U_NONLINEAR = 75.0   # RHS 31 + assembly 8 + factor 4 + solve 5 + coupling 27
+FLOP_Z = 20.0             # RHS 8 + spread 4 + prefactored solve 5 + interpolation 3
+FLOP_EXCITATION = 30.0    # per string-step with a hammer or bow (scalar solve + update)
+FLOP_RESPONSE_U = 10.0    # per transverse row for the unit-force response (nonlinear, forced)
+
+
+def algorithmic_flops(strings, grids) -> float:
+    tot = 0.0
+    for d, (nt, nl) in zip(strings, grids):
+        n_u = nt - 1
+        linear = d["alpha"] == 1.0
+        n_z = 0 if linear else max(nl - 1, 0)
+        per = n_u * (FLOP_U_LINEAR if linear else FLOP_U_NONLINEAR) + n_z * FLOP_Z
+        if d["excitation"]["kind"] != "pluck":
+            per += FLOP_EXCITATION + (0.0 if linear else n_u * FLOP_RESPONSE_U)
+        tot += per * (d["n_samples"] - 2)
+    return tot
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup(n_gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value: float) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_rate(strings, n_samples: int, threads: int = 0):
+    """Time the FP64 oracle (OpenMP over strings) on `strings` x n_samples."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    _, used = oracle.run_batch(strings, n_samples=n_samples, threads=threads)
+    dt = time.perf_counter() - t0
+    return len(strings) * n_samples / dt, used, dt
+
+
+WORKLOAD_NAME = ("256 strings x 2 s at 48 kHz: f0 log-U[40,1000] Hz, kappa U[0.5,3], alpha U[1,10], "
+                 "sigma0 U[0.1,2], sigma1 U[1e-6,1e-4], pluck/hammer/bow uniform (seed 2)")
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    strings = W.batch_mixed(args.strings, seconds=args.seconds, seed=2)
+    sample = strings[: args.ref_strings]
+    n = args.ref_samples
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sample, n)
+    rates, used, dts = [], 0, []
+    for _ in range(args.steps):
+        r, used, dt = cpu_oracle_rate(sample, n)
+        rates.append(r)
+        dts.append(dt)
+    value = len(sample) * n * len(dts) / sum(dts)
+    desc = f"first {len(sample)} strings of the workload x {n} samples each per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "reference": "FP64 CPU oracle (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 1 << 30)
+    strings = W.batch_mixed(args.strings, seconds=args.seconds, seed=2 + 1000 * rank)
+    ns = np.array([d["n_samples"] for d in strings], dtype=np.int64)
+    offs = np.zeros(len(ns), dtype=np.int64)
+    offs[1:] = np.cumsum(ns)[:-1]
+    total = int(ns.sum())
+    out = torch.empty(total, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 18, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def make_batch():
+        hs = [sfd.string_from_dict(ctx, d) for d in strings]
+        return hs, sfd.sfd_batch_create(ctx, hs)
+
+    def free_batch(hb):
+        hs, b = hb
+        sfd.sfd_batch_destroy(b)
+        for h in hs:
+            sfd.sfd_string_destroy(h)
+
+    grids = []   # grid sizes as the library derived them
+    for d in strings:
+        h = sfd.string_from_dict(ctx, d)
+        nt, nl, _, _ = sfd.sfd_string_info(h)
+        grids.append((nt, nl))
+        sfd.sfd_string_destroy(h)
+    flops = algorithmic_flops(strings, grids)
+    updates = sum(((nt - 1) + (0 if d["alpha"] == 1.0 else max(nl - 1, 0))) * (d["n_samples"] - 2)
+                  for d, (nt, nl) in zip(strings, grids))
+
+    # warm-up
+    for _ in range(args.warmup):
+        hb = make_batch()
+        sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+        torch.cuda.synchronize(dev)
+        free_batch(hb)
+    # timed: inputs for every step created before the region
+    batches = [make_batch() for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    launches = 0
+    for i, hb in enumerate(batches):
+        flush.zero_()
+        ev[i][0].record(stream)
+        sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+        ev[i][1].record(stream)
+        launches += sfd.sfd_last_launch_count(ctx)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    y = out[: min(total, 1 << 20)].float().cpu().numpy()
+    finite = bool(np.all(np.isfinite(y)))
+    for hb in batches:
+        free_batch(hb)
+    t_total = max_over_ranks(ws, sum(times_ms) / 1e3)
+    value = ws * total * args.steps / t_total
+    ms_step = 1e3 * t_total / args.steps
+
+    # e2e through the public API with host buffers (create -> synthesize to
+    # pinned host memory -> destroy), wall-clock per step
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(total, dtype=torch.float32).pin_memory()
+        h0, d0 = sfd.sfd_ctx_transfer_bytes(ctx)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            hs = [sfd.string_from_dict(ctx, d) for d in strings]
+            b = sfd.sfd_batch_create(ctx, hs)
+            sfd.lib().sfd_batch_synthesize_host(
+                b, ns.ctypes.data_as(sfd.ctypes.POINTER(sfd.ctypes.c_int64)), host_out.data_ptr(),
+                offs.ctypes.data_as(sfd.ctypes.POINTER(sfd.ctypes.c_int64)), None)
+            sfd.sfd_batch_destroy(b)
+            for h in hs:
+                sfd.sfd_string_destroy(h)
+        torch.cuda.synchronize(dev)
+        dt = max_over_ranks(ws, time.perf_counter() - t0)
+        h1, d1 = sfd.sfd_ctx_transfer_bytes(ctx)
+        e2e = {"value": ws * total * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int((h1 - h0) / args.e2e_steps),
+               "d2h_bytes_per_step": int((d1 - d0) / args.e2e_steps)}
+    sfd.sfd_ctx_destroy(ctx)
+
+    if rank != 0:
+        return 0
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    avg_launch_s = sum(times_ms) / len(times_ms) / 1e3
+    achieved = flops / avg_launch_s / 1e12
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        sample = strings[: args.cpu_strings]
+        rate, used, dt = cpu_oracle_rate(sample, args.cpu_samples)
+        cpu = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"first {len(sample)} strings of the workload x {args.cpu_samples} samples "
+                         f"({dt:.1f} s wall)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "strings": args.strings, "seconds": args.seconds, "fs": FS,
+                   "samples_per_step": total, "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": "one persistent kernel per step, one warp per string"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+        "grid_point_updates_per_s": ws * updates * args.steps / t_total,
+        "realtime_factor": ws * total / FS * args.steps / t_total,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "outputs_finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--strings", type=int, default=256)
+    ap.add_argument("--seconds", type=float, default=2.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-strings", type=int, default=64)
+    ap.add_argument("--cpu-samples", type=int, default=12000)
+    ap.add_argument("--ref-strings", type=int, default=32)
+    ap.add_argument("--ref-samples", type=int, default=4800)
+    args = ap.parse_args(argv)
+    ws, rank, local = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ws, rank)
+        return run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * sfd.h - C-ABI of the GB300 (sm_103a) nonlinear planar stiff-string
+ * synthesizer: batched FP32 time-stepping of the finite-difference scheme of
+ * "String Sound Synthesizer on GPU-Accelerated Finite Difference Scheme"
+ * (Lee, Choi, Lee, arXiv 2311.18505).
+ *
+ * What one step computes (Sec. 3.2, Eq. 4; matrix form Sec. 3.4, Eqs. 7-9):
+ *   transverse u (N_t intervals) and longitudinal zeta (N_l intervals) are
+ *   advanced from (w^{n-1}, w^n) to w^{n+1} by the linearly-implicit scheme
+ *     Theta delta_tt u = g^2 d_xx u - kappa^2 d_xxxx u
+ *                      + g^2 (alpha^2-1)/2 d_x+ (q^2 mu_t. q + 2 q mu_tt p)
+ *                      - 2 sigma0 delta_t. u + 2 sigma1 delta_t. d_xx u + F J
+ *     delta_tt z = g^2 alpha^2 d_xx z + g^2 (alpha^2-1)/2 d_x+ I_(t->l)(q mu_t. q)
+ *                      - 2 sigma0 delta_t. z + 2 sigma1 delta_t. d_xx z
+ *   with a pluck initial condition, a hammer (Sec. 3.3.2, Eq. 6) or a bow
+ *   (Sec. 3.3.1, Eq. 5) force F at one point, and one output sample per step
+ *   read at the pickup.  Grids follow the spacing rules of Sec. 3.2.
+ *
+ * Units.  Parameters are SI at this boundary.  Internally x is normalised
+ * to [0,1] and displacements by the length L (Table 1: gamma =
+ * L^-1 sqrt(T0 / rho A), so f0 = gamma / 2, Sec. 4.1).  Output samples are
+ * transverse displacement at the pickup in metres, FP32.
+ *
+ * Ownership.  The library owns every ctx, string and batch object and all
+ * device memory behind them (carved from the context's device-memory pool).
+ * The caller owns its output buffers (host memory, or device memory on the
+ * context's device, e.g. a torch tensor's data pointer).
+ *
+ * Errors.  Every call returns an sfd_status; nothing aborts.  On error the
+ * thread-local message of sfd_last_error() says why.  A string whose state
+ * became non-finite reports SFD_EUNSTABLE from then on.
+ *
+ * Threading.  Objects are not thread-safe; distinct contexts may be used
+ * from distinct threads.  Calls on one context are ordered on its stream.
+ */
+#ifndef SFD_H
+#define SFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sfd_status;
+enum {
+  SFD_OK = 0,
+  SFD_EINVAL = -1,     /* invalid argument or parameter                     */
+  SFD_ENOMEM = -2,     /* device-memory pool exhausted                      */
+  SFD_EUNSTABLE = -3,  /* state became non-finite                           */
+  SFD_ENOCONV = -4,    /* coupled solve hit its sweep cap (result kept)     */
+  SFD_ECUDA = -5,      /* CUDA runtime error                                */
+  SFD_ETIMEOUT = -6,   /* bounded wait expired                              */
+  SFD_EBUSY = -7,      /* object in use (e.g. string inside a live batch)   */
+  SFD_ESTATE = -8      /* call not valid in the current state               */
+};
+
+enum { SFD_BOUNDARY_CLAMPED = 0, SFD_BOUNDARY_SIMPLY_SUPPORTED = 1 };
+enum { SFD_GRID_THETA_BOUND = 0, SFD_GRID_PRINTED = 1 };
+enum { SFD_MOD_NONE = 0, SFD_MOD_VIBRATO = 1, SFD_MOD_GLISS = 2 };
+
+typedef struct sfd_ctx sfd_ctx;
+typedef struct sfd_string sfd_string;
+typedef struct sfd_batch sfd_batch;
+
+/* String parameters (Table 1).  Zero-initialise and set what you need;
+ * sfd_params_default() fills the defaults listed below. */
+typedef struct {
+  double f0;              /* Hz; gamma = 2 f0 (Sec. 4.1).  Ignored if gamma > 0 */
+  double gamma;           /* wave speed [1/s]                                    */
+  double kappa;           /* stiffness [1/s] (Table 1, Eq. 4)                    */
+  double alpha;           /* stiffness-to-tension ratio, >= 1 (Table 1)          */
+  double sigma0;          /* frequency-independent loss [1/s] (Eq. 4)            */
+  double sigma1;          /* frequency-dependent loss (Eq. 4)                     */
+  double length_m;        /* L [m], default 1                                     */
+  double fs;              /* sample rate [Hz], default 48000; k = 1/fs (Sec. 3)   */
+  double linear_density;  /* rho A [kg/m], default 5e-3; maps N and kg to the
+                             normalised equations                                 */
+  double theta;           /* theta-scheme parameter, default (1+4/pi^2)/2 (Sec. 3.2) */
+  int32_t boundary;       /* SFD_BOUNDARY_*, default clamped (Sec. 4.1)           */
+  int32_t grid_rule;      /* SFD_GRID_*: 0 (default) sizes N_t by the stability
+                             bound of the theta actually used; 1 uses the printed
+                             h_t of Sec. 3.2, which is that bound for theta = 1   */
+  double pickup_pos;      /* output point, fraction of L, default 0.7             */
+  double f0_max_ratio;    /* >= 1: grids sized for gamma * ratio (modulation peak) */
+} sfd_string_params;
+
+/* Fill p with the defaults (f0 = 110, kappa = 1, alpha = 1, sigma0 = 0.5,
+ * sigma1 = 1e-5, L = 1 m, fs = 48 kHz, rho A = 5e-3, theta = (1+4/pi^2)/2,
+ * clamped, theta-bound grid, pickup 0.7, ratio 1). */
+void sfd_params_default(sfd_string_params* p);
+
+/* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * (NULL: the legacy default stream).  mem_budget_bytes sizes the device pool
+ * that holds every string's state (0: 256 MiB).  *out receives the ctx. */
+sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes, sfd_ctx** out);
+void sfd_ctx_destroy(sfd_ctx* ctx);
+
+/* Pool accounting: bytes in use and total. */
+sfd_status sfd_ctx_memory(const sfd_ctx* ctx, size_t* used, size_t* total);
+
+/* Create a string from parameters: derives N_t from the transverse stability
+ * bound and N_l = floor(1 / (gamma alpha k)) (Sec. 3.2), allocates its state
+ * and sets it at rest at time level n = 1.  SFD_EINVAL on bad parameters,
+ * SFD_ENOMEM when the pool is full. */
+sfd_status sfd_string_create(sfd_ctx* ctx, const sfd_string_params* p, sfd_string** out);
+
+/* Grid of a string: intervals N_t, N_l and spacings h_t = 1/N_t, h_l = 1/N_l. */
+sfd_status sfd_string_info(const sfd_string* s, int32_t* n_t, int32_t* n_l, double* h_t, double* h_l);
+
+/* Pluck (Sec. 3.3): initial condition u^0 = u^1 = triangle of peak amp/L at
+ * pos (fraction of L), zero initial velocity.  Valid only before the first
+ * synthesize call (else SFD_ESTATE). */
+sfd_status sfd_excite_pluck(sfd_string* s, double amp_m, double pos);
+
+/* Hammer (Sec. 3.3.2, Eq. 6): lumped mass m_H hitting at pos with velocity
+ * vel from the string's rest position; contact force
+ *   F_H = omega_H^{1+alpha_H} [eta]_+^{alpha_H-1} mu_t. eta,  eta = u_H - I u,
+ * mass ratio M = m_H / (rho A L).  Before the first synthesize call only. */
+sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, double pos,
+                             double omega_h, double alpha_h);
+
+/* Bow (Sec. 3.3.1, Eq. 5): force F_B [N] and speed v_B [m/s] at pos with
+ * friction phi(v) = sign(v)(eps + (1-eps) e^{-a |v|}), a in s/m; the force
+ * drops to zero from release_time_s on (< 0: never).  Sticking (|v_rel| = 0)
+ * is taken whenever it is consistent.  Before the first synthesize call. */
+sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double pos,
+                          double a_s_per_m, double eps, double release_time_s);
+
+/* f0 modulation (Sec. 1): kind SFD_MOD_VIBRATO, gamma^n = gamma 2^{(c/1200)
+ * sin(2 pi rate t + phase)} with depth c in cents; SFD_MOD_GLISS, gamma^n =
+ * gamma 2^{D t / duration} with depth D in octaves.  The grid must have been
+ * sized for the peak (f0_max_ratio), else SFD_EINVAL. */
+sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth,
+                              double phase_rad, double duration_s);
+
+/* Produce the next n_samples output samples y^j = L I(x_o) u^j (j counts
+ * from 0, so the first two samples are the initial levels).  out is host
+ * memory (out_on_device = 0) or device memory on the context's device.
+ * Calls are resumable: synthesize(a) then synthesize(b) equals
+ * synthesize(a + b).  Blocks until the samples are in `out`. */
+sfd_status sfd_synthesize(sfd_string* s, int64_t n_samples, float* out, int32_t out_on_device);
+
+/* Time level n and next output index of a string. */
+sfd_status sfd_string_position(const sfd_string* s, int64_t* time_level, int64_t* next_sample);
+
+/* Copy the state to host FP32 arrays: u^{n-1}, u^n (N_t - 1 each),
+ * z^{n-1}, z^n (N_l - 1 each, may be NULL) in normalised units. */
+sfd_status sfd_string_state(const sfd_string* s, float* u_prev, float* u, float* z_prev, float* z);
+
+/* Solver statistics of a string since creation: status (SFD_OK,
+ * SFD_EUNSTABLE, SFD_ENOCONV), the largest and the total number of
+ * Gauss-Seidel sweeps of the coupled transverse/longitudinal solve. */
+sfd_status sfd_string_stats(const sfd_string* s, int32_t* status, int32_t* max_sweeps, int64_t* total_sweeps);
+
+sfd_status sfd_string_destroy(sfd_string* s);
+
+/* Batched form: n strings advanced together by one launch of the persistent
+ * step kernel.  Strings stay owned by the caller's handles; a string in a
+ * live batch cannot be destroyed (SFD_EBUSY). */
+sfd_status sfd_batch_create(sfd_ctx* ctx, int32_t n, sfd_string* const* strings, sfd_batch** out);
+
+/* Advance string i by n_samples[i] samples into out_device + out_offsets[i]
+ * (device memory, FP32).  One launch of the persistent step kernel on the
+ * ctx's stream; the call returns once it is queued, unless
+ * per_string_status (host, may be NULL) is given, in which case it waits
+ * and writes each string's status (SFD_OK, SFD_EUNSTABLE, SFD_ENOCONV). */
+sfd_status sfd_batch_synthesize(sfd_batch* b, const int64_t* n_samples, float* out_device,
+                                const int64_t* out_offsets, int32_t* per_string_status);
+
+/* Same, with host output: copies the samples to out_host after the launch. */
+sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, float* out_host,
+                                     const int64_t* out_offsets, int32_t* per_string_status);
+
+/* Number of kernel launches issued by the last batch/synthesize call. */
+int32_t sfd_last_launch_count(const sfd_ctx* ctx);
+
+/* Cumulative bytes the library copied host->device and device->host on this
+ * context (state uploads, job tables, outputs, status reads). */
+sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint64_t* d2h_total);
+
+sfd_status sfd_batch_destroy(sfd_batch* b);
+
+/* Thread-local message describing the last error. */
+const char* sfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

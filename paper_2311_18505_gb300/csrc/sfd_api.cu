@@ -1,0 +1,811 @@
+// C-ABI runtime of the string synthesizer (include/sfd.h): contexts with a
+// device-memory pool, strings (grid + coefficient derivation in FP64, state
+// in the pool), excitations, batches and the launch of the step kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sfd.h"
+#include "sfd_types.h"
+
+namespace sfd {
+cudaError_t launch_synth(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta,
+                         int n_ctas, cudaStream_t stream);
+}
+
+using namespace sfd;
+
+namespace {
+
+thread_local std::string g_err;
+
+sfd_status fail(sfd_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+sfd_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SFD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SFD_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr double kPi = 3.14159265358979323846;
+
+// First-fit allocator over one device allocation.
+class Pool {
+ public:
+  sfd_status init(size_t bytes) {
+    size_ = (bytes + kAlign - 1) / kAlign * kAlign;
+    cudaError_t e = cudaMalloc(&base_, size_);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(pool)");
+    free_[0] = size_;
+    return SFD_OK;
+  }
+  void release() {
+    if (base_) cudaFree(base_);
+    base_ = nullptr;
+  }
+  char* alloc(size_t bytes) {
+    bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        used_ += bytes;
+        live_[off] = bytes;
+        return base_ + off;
+      }
+    }
+    return nullptr;
+  }
+  void dealloc(char* p) {
+    if (!p) return;
+    const size_t off = static_cast<size_t>(p - base_);
+    auto lit = live_.find(off);
+    if (lit == live_.end()) return;
+    size_t sz = lit->second;
+    live_.erase(lit);
+    used_ -= sz;
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + sz) {
+      sz += nx->second;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(off);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second == off) {
+        start = pv->first;
+        sz += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[start] = sz;
+  }
+  size_t used() const { return used_; }
+  size_t size() const { return size_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t size_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_, live_;
+};
+
+}  // namespace
+
+struct sfd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Pool pool;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  Job* d_jobs = nullptr;
+  int job_cap = 0;
+  int* d_counter = nullptr;
+  int last_launches = 0;
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;   // all host<->device copies made
+};
+
+struct sfd_string {
+  sfd_ctx* ctx = nullptr;
+  sfd_string_params p{};
+  double gamma = 0, k = 0;
+  int n_t = 0, n_l = 0;
+  Desc h{};                 // host copy of the descriptor
+  char* block = nullptr;    // pool block: Desc | Scalars | u du z dz xz az
+  Desc* d_desc = nullptr;
+  Scalars* d_sc = nullptr;
+  bool started = false;     // first synthesize done
+  int batch_refs = 0;
+  // excitation (kept to rebuild the initial state)
+  int exc = kPluck;
+  double pluck_amp = 0, pluck_pos = 0.5;
+  double hammer_uh1 = 0;    // u_H^1 = v_H k (normalised), u_H^0 = 0
+};
+
+struct sfd_batch {
+  sfd_ctx* ctx = nullptr;
+  std::vector<sfd_string*> strings;
+};
+
+namespace {
+
+sfd_status set_device(const sfd_ctx* c) {
+  SFD_CUDA(cudaSetDevice(c->device));
+  return SFD_OK;
+}
+
+cudaError_t h2d(sfd_ctx* c, void* dst, const void* src, size_t n) {
+  c->h2d_bytes += n;
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream);
+}
+
+cudaError_t d2h(sfd_ctx* c, void* dst, const void* src, size_t n) {
+  c->d2h_bytes += n;
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream);
+}
+
+// Transverse and longitudinal grids from the spacing rules (Sec. 3.2).
+// Rule 0 keeps g^2 k^2 / h^2 + 4 kappa^2 k^2 / h^4 <= 2 theta - 1 (von
+// Neumann bound of the theta-scheme); rule 1 is the printed h_t, i.e. the
+// same bound with theta = 1.  h_l >= g alpha k.  N = floor(1 / h_min), with
+// a 1e-12 relative slack so exact ratios do not round down.
+sfd_status derive_grid(const sfd_string_params& p, double gamma_max, int* n_t, int* n_l) {
+  const double k = 1.0 / p.fs;
+  const double a = gamma_max * gamma_max * k * k;
+  const double b = p.kappa * p.kappa * k * k;
+  double h2;
+  if (p.grid_rule == SFD_GRID_PRINTED) {
+    h2 = 0.5 * (a + std::sqrt(a * a + 16.0 * b));
+  } else {
+    const double d = 2.0 * p.theta - 1.0;
+    h2 = (a + std::sqrt(a * a + 16.0 * d * b)) / (2.0 * d);
+  }
+  const double nt = std::floor((1.0 / std::sqrt(h2)) * (1.0 + 1e-12));
+  const double nl = std::floor((1.0 / (gamma_max * p.alpha * k)) * (1.0 + 1e-12));
+  if (!(nt >= 2.0)) return fail(SFD_EINVAL, "transverse grid has fewer than 2 intervals (f0 too high for fs)");
+  if (nt > 4000.0) return fail(SFD_EINVAL, "transverse grid too fine (N_t = %.0f > 4000)", nt);
+  if (nl > 16000.0) return fail(SFD_EINVAL, "longitudinal grid too fine (N_l = %.0f > 16000)", nl);
+  *n_t = static_cast<int>(nt);
+  *n_l = nl < 1.0 ? 1 : static_cast<int>(nl);
+  return SFD_OK;
+}
+
+int rows_per_lane(int n) {  // odd m with 32 m >= n + 1
+  int m = (n + 1 + kWarp - 1) / kWarp;
+  if (m < 1) m = 1;
+  if ((m & 1) == 0) ++m;
+  return m;
+}
+
+void point_weights(int n_t, double x, int32_t* node, float* w) {
+  double pos = x * n_t;
+  int l = static_cast<int>(std::floor(pos));
+  if (l < 0) l = 0;
+  if (l > n_t - 1) l = n_t - 1;
+  *node = l;
+  *w = static_cast<float>(pos - l);
+}
+
+double n_l_sq(const sfd_string* s) { return static_cast<double>(s->n_l) * s->n_l; }
+
+// Coefficients of the acceleration-form update (see sfd_kernel.cu), FP64 -> FP32.
+void fill_desc(sfd_string* s) {
+  const sfd_string_params& p = s->p;
+  Desc& D = s->h;
+  const double k = s->k, g = s->gamma;
+  const double ht = 1.0 / s->n_t, hl = 1.0 / s->n_l;
+  D.n_t = s->n_t;
+  D.n_l = s->n_l;
+  D.n_u = s->n_t - 1;
+  D.linear = (p.alpha == 1.0) ? 1 : 0;
+  D.n_z = (!D.linear && s->n_l > 1) ? s->n_l - 1 : 0;
+  D.m_u = rows_per_lane(D.n_u);
+  D.m_z = D.n_z > 0 ? rows_per_lane(D.n_z) : 0;
+  // The longitudinal block (1 + s0) I - s1l d2 is nearly diagonal for string
+  // losses: fold its off-diagonal into the Gauss-Seidel sweeps (Jacobi
+  // contraction 2 s1l / (1 + s0 + 2 s1l)) when that ratio is small.
+  {
+    const double s1l = p.sigma1 * k * n_l_sq(s);
+    D.z_jacobi = (2.0 * s1l / (1.0 + p.sigma0 * k + 2.0 * s1l) <= 0.01) ? 1 : 0;
+  }
+  D.boundary = p.boundary;
+  D.th = static_cast<float>(p.theta);
+  D.tho = static_cast<float>(0.5 * (1.0 - p.theta));
+  D.s0 = static_cast<float>(p.sigma0 * k);
+  D.s1 = static_cast<float>(p.sigma1 * k / (ht * ht));
+  D.s1l = static_cast<float>(p.sigma1 * k / (hl * hl));
+  D.lam2 = static_cast<float>(g * g * k * k / (ht * ht));
+  D.mu2 = static_cast<float>(p.kappa * p.kappa * k * k / (ht * ht * ht * ht));
+  D.lam2l = static_cast<float>(g * g * p.alpha * p.alpha * k * k / (hl * hl));
+  const double phi = 0.5 * g * g * (p.alpha * p.alpha - 1.0);   // phi' of Eq. 4
+  D.ca = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht * ht));
+  D.cb = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht));
+  D.cz = static_cast<float>(phi * k * k / (2.0 * ht * ht * hl));
+  D.out_scale = static_cast<float>(p.length_m);
+  point_weights(s->n_t, p.pickup_pos, &D.o_node, &D.o_w);
+  D.jscale = static_cast<float>(s->n_t);
+  D.k = static_cast<float>(k);
+  D.k2 = static_cast<float>(k * k);
+  D.exc = s->exc;
+}
+
+size_t block_bytes(const Desc& D) {
+  size_t b = 0;
+  auto take = [&](size_t n) { b = (b + kAlign - 1) / kAlign * kAlign + n; };
+  take(sizeof(Desc));
+  take(sizeof(Scalars));
+  take(sizeof(float) * D.n_u);
+  take(sizeof(float) * D.n_u);
+  for (int a = 0; a < 4; ++a) take(sizeof(float) * (D.n_z > 0 ? D.n_z : 1));
+  return (b + kAlign - 1) / kAlign * kAlign;
+}
+
+void carve(sfd_string* s) {
+  size_t b = 0;
+  auto take = [&](size_t n) {
+    b = (b + kAlign - 1) / kAlign * kAlign;
+    char* p = s->block + b;
+    b += n;
+    return p;
+  };
+  Desc& D = s->h;
+  s->d_desc = reinterpret_cast<Desc*>(take(sizeof(Desc)));
+  s->d_sc = reinterpret_cast<Scalars*>(take(sizeof(Scalars)));
+  const size_t nz = D.n_z > 0 ? D.n_z : 1;
+  D.u = reinterpret_cast<float*>(take(sizeof(float) * D.n_u));
+  D.du = reinterpret_cast<float*>(take(sizeof(float) * D.n_u));
+  D.z = reinterpret_cast<float*>(take(sizeof(float) * nz));
+  D.dz = reinterpret_cast<float*>(take(sizeof(float) * nz));
+  D.xz = reinterpret_cast<float*>(take(sizeof(float) * nz));
+  D.az = reinterpret_cast<float*>(take(sizeof(float) * nz));
+  D.sc = s->d_sc;
+}
+
+// Upload the descriptor and the initial state (w^0, w^1 of Sec. 3.4).
+sfd_status upload_initial(sfd_string* s) {
+  const Desc& D = s->h;
+  std::vector<float> u(D.n_u, 0.f), du(D.n_u, 0.f);
+  const size_t nz = D.n_z > 0 ? D.n_z : 1;
+  std::vector<float> zero(nz, 0.f);
+  Scalars sc{};
+  sc.n = 1;
+  sc.next_out = 0;
+  if (s->exc == kPluck && s->pluck_amp != 0.0) {
+    const double c0 = s->pluck_amp / s->p.length_m, xp = s->pluck_pos;
+    for (int l = 1; l < s->n_t; ++l) {
+      const double x = static_cast<double>(l) / s->n_t;
+      u[l - 1] = static_cast<float>(x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp));
+    }
+  }
+  if (s->exc == kHammer) {
+    // the hammer starts at the string's rest position moving with v_H
+    sc.uh = static_cast<float>(s->hammer_uh1);
+    sc.duh = static_cast<float>(s->hammer_uh1);
+  }
+  sfd_ctx* c = s->ctx;
+  SFD_CUDA(h2d(c, s->d_desc, &s->h, sizeof(Desc)));
+  SFD_CUDA(h2d(c, s->d_sc, &sc, sizeof(Scalars)));
+  SFD_CUDA(h2d(c, D.u, u.data(), sizeof(float) * D.n_u));
+  SFD_CUDA(h2d(c, D.du, du.data(), sizeof(float) * D.n_u));
+  SFD_CUDA(h2d(c, D.z, zero.data(), sizeof(float) * nz));
+  SFD_CUDA(h2d(c, D.dz, zero.data(), sizeof(float) * nz));
+  SFD_CUDA(h2d(c, D.xz, zero.data(), sizeof(float) * nz));
+  SFD_CUDA(h2d(c, D.az, zero.data(), sizeof(float) * nz));
+  SFD_CUDA(cudaStreamSynchronize(c->stream));
+  return SFD_OK;
+}
+
+sfd_status ensure_jobs(sfd_ctx* c, int n) {
+  if (n <= c->job_cap) return SFD_OK;
+  if (c->d_jobs) cudaFree(c->d_jobs);
+  c->d_jobs = nullptr;
+  int cap = std::max(n, 64);
+  SFD_CUDA(cudaMalloc(&c->d_jobs, sizeof(Job) * cap));
+  c->job_cap = cap;
+  return SFD_OK;
+}
+
+double job_cost(const sfd_string* s, int64_t n) {
+  const Desc& D = s->h;
+  double per = D.m_u * 3.0 + 40.0;
+  if (D.n_z > 0) per += 4.0 * (D.m_u + D.m_z + 40.0);
+  if (s->exc != kPluck) per *= 1.5;
+  return per * static_cast<double>(n);
+}
+
+// Queue one launch of the persistent kernel over `jobs` (host array).
+sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners) {
+  c->last_launches = 0;
+  if (jobs.empty()) return SFD_OK;
+  // longest jobs first: the work queue hands them out in this order
+  std::vector<int> order(jobs.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+  std::vector<double> cost(jobs.size());
+  int wf = 0;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    cost[i] = job_cost(owners[i], jobs[i].n_samples);
+    wf = std::max(wf, warp_smem_floats(owners[i]->h.m_u, owners[i]->h.m_z));
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<Job> sorted(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) sorted[i] = jobs[order[i]];
+  sfd_status rc = ensure_jobs(c, static_cast<int>(sorted.size()));
+  if (rc) return rc;
+  SFD_CUDA(h2d(c, c->d_jobs, sorted.data(), sizeof(Job) * sorted.size()));
+  const size_t wbytes = static_cast<size_t>(wf) * sizeof(float);
+  if (wbytes > c->smem_optin)
+    return fail(SFD_EINVAL, "string too large for one warp's shared memory (%zu > %zu bytes)", wbytes,
+                c->smem_optin);
+  const int n_jobs = static_cast<int>(sorted.size());
+  int wpc = static_cast<int>(std::min<size_t>(4, c->smem_optin / wbytes));
+  // spread warps over all SMs before stacking them
+  const int per_sm = (n_jobs + c->sm_count - 1) / c->sm_count;
+  wpc = std::max(1, std::min(wpc, per_sm));
+  if (const char* env = getenv("SFD_WARPS_PER_CTA")) {
+    int v = atoi(env);
+    if (v >= 1 && v <= 4 && static_cast<size_t>(v) * wbytes <= c->smem_optin) wpc = v;
+  }
+  const size_t cta_bytes = wbytes * wpc;
+  int ctas_per_sm = static_cast<int>(std::max<size_t>(1, (228u * 1024u) / (cta_bytes + 1024)));
+  ctas_per_sm = std::min(ctas_per_sm, 16);
+  int n_ctas = std::min((n_jobs + wpc - 1) / wpc, c->sm_count * ctas_per_sm);
+  cudaError_t e = launch_synth(c->d_jobs, n_jobs, c->d_counter, wf, wpc, n_ctas, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launch_synth");
+  c->last_launches = 1;
+  return SFD_OK;
+}
+
+sfd_status read_status(const sfd_string* s, Scalars* out) {
+  SFD_CUDA(d2h(s->ctx, out, s->d_sc, sizeof(Scalars)));
+  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return SFD_OK;
+}
+
+sfd_status status_code(const Scalars& sc) {
+  if (sc.status & kStUnstable) return SFD_EUNSTABLE;
+  if (sc.status & kStNoConv) return SFD_ENOCONV;
+  return SFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sfd_params_default(sfd_string_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->f0 = 110.0;
+  p->kappa = 1.0;
+  p->alpha = 1.0;
+  p->sigma0 = 0.5;
+  p->sigma1 = 1e-5;
+  p->length_m = 1.0;
+  p->fs = 48000.0;
+  p->linear_density = 5e-3;
+  p->theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
+  p->boundary = SFD_BOUNDARY_CLAMPED;
+  p->grid_rule = SFD_GRID_THETA_BOUND;
+  p->pickup_pos = 0.7;
+  p->f0_max_ratio = 1.0;
+}
+
+const char* sfd_last_error(void) { return g_err.c_str(); }
+
+sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes, sfd_ctx** out) {
+  if (!out) return fail(SFD_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return fail(SFD_ECUDA, "no CUDA device available");
+  if (device < 0 || device >= ndev) return fail(SFD_EINVAL, "device %d out of range", device);
+  sfd_ctx* c = new (std::nothrow) sfd_ctx();
+  if (!c) return fail(SFD_ENOMEM, "host allocation failed");
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) { delete c; return cuda_fail(e, "cudaSetDevice"); }
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) { delete c; return cuda_fail(e, "props"); }
+  if (prop.major * 10 + prop.minor < 100) {
+    delete c;
+    return fail(SFD_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major,
+                prop.minor);
+  }
+  c->sm_count = prop.multiProcessorCount;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  sfd_status rc = c->pool.init(mem_budget_bytes ? mem_budget_bytes : (size_t{256} << 20));
+  if (rc) { delete c; return rc; }
+  if ((e = cudaMalloc(&c->d_counter, sizeof(int))) != cudaSuccess) {
+    c->pool.release();
+    delete c;
+    return cuda_fail(e, "cudaMalloc(counter)");
+  }
+  *out = c;
+  return SFD_OK;
+}
+
+void sfd_ctx_destroy(sfd_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->pool.release();
+  if (c->d_jobs) cudaFree(c->d_jobs);
+  if (c->d_counter) cudaFree(c->d_counter);
+  delete c;
+}
+
+sfd_status sfd_ctx_memory(const sfd_ctx* c, size_t* used, size_t* total) {
+  if (!c) return fail(SFD_EINVAL, "ctx is NULL");
+  if (used) *used = c->pool.used();
+  if (total) *total = c->pool.size();
+  return SFD_OK;
+}
+
+int32_t sfd_last_launch_count(const sfd_ctx* c) { return c ? c->last_launches : 0; }
+
+sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* c, uint64_t* h2d_total, uint64_t* d2h_total) {
+  if (!c) return fail(SFD_EINVAL, "ctx is NULL");
+  if (h2d_total) *h2d_total = c->h2d_bytes;
+  if (d2h_total) *d2h_total = c->d2h_bytes;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_create(sfd_ctx* c, const sfd_string_params* p, sfd_string** out) {
+  if (!c || !p || !out) return fail(SFD_EINVAL, "NULL argument");
+  *out = nullptr;
+  sfd_string_params q = *p;
+  if (q.length_m == 0) q.length_m = 1.0;
+  if (q.fs == 0) q.fs = 48000.0;
+  if (q.linear_density == 0) q.linear_density = 5e-3;
+  if (q.theta == 0) q.theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
+  if (q.pickup_pos == 0) q.pickup_pos = 0.7;
+  if (q.f0_max_ratio < 1.0) q.f0_max_ratio = 1.0;
+  const double gamma = q.gamma > 0 ? q.gamma : 2.0 * q.f0;
+  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(SFD_EINVAL, "f0/gamma must be > 0");
+  if (!(q.fs > 0)) return fail(SFD_EINVAL, "fs must be > 0");
+  if (!(q.kappa >= 0)) return fail(SFD_EINVAL, "kappa must be >= 0");
+  if (!(q.alpha >= 1.0)) return fail(SFD_EINVAL, "alpha must be >= 1");
+  if (!(q.sigma0 >= 0) || !(q.sigma1 >= 0)) return fail(SFD_EINVAL, "losses must be >= 0");
+  if (!(q.theta > 0.5 && q.theta <= 1.0)) return fail(SFD_EINVAL, "theta must be in (1/2, 1]");
+  if (!(q.pickup_pos > 0 && q.pickup_pos < 1)) return fail(SFD_EINVAL, "pickup must be in (0, 1)");
+  if (!(q.length_m > 0) || !(q.linear_density > 0)) return fail(SFD_EINVAL, "length and density must be > 0");
+  if (q.boundary != 0 && q.boundary != 1) return fail(SFD_EINVAL, "bad boundary");
+  if (q.grid_rule != 0 && q.grid_rule != 1) return fail(SFD_EINVAL, "bad grid rule");
+  int n_t = 0, n_l = 0;
+  sfd_status rc = derive_grid(q, gamma * q.f0_max_ratio, &n_t, &n_l);
+  if (rc) return rc;
+  sfd_string* s = new (std::nothrow) sfd_string();
+  if (!s) return fail(SFD_ENOMEM, "host allocation failed");
+  s->ctx = c;
+  s->p = q;
+  s->gamma = gamma;
+  s->k = 1.0 / q.fs;
+  s->n_t = n_t;
+  s->n_l = n_l;
+  s->exc = kPluck;
+  s->h.bow_release_n = INT64_MAX;
+  fill_desc(s);
+  const size_t wbytes = static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z)) * sizeof(float);
+  if (wbytes > c->smem_optin) {
+    delete s;
+    return fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", n_t, n_l);
+  }
+  if ((rc = set_device(c))) { delete s; return rc; }
+  s->block = c->pool.alloc(block_bytes(s->h));
+  if (!s->block) {
+    delete s;
+    return fail(SFD_ENOMEM, "device pool exhausted (%zu of %zu bytes used)", c->pool.used(), c->pool.size());
+  }
+  carve(s);
+  if ((rc = upload_initial(s))) {
+    c->pool.dealloc(s->block);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_info(const sfd_string* s, int32_t* n_t, int32_t* n_l, double* h_t, double* h_l) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (n_t) *n_t = s->n_t;
+  if (n_l) *n_l = s->n_l;
+  if (h_t) *h_t = 1.0 / s->n_t;
+  if (h_l) *h_l = 1.0 / s->n_l;
+  return SFD_OK;
+}
+
+sfd_status sfd_excite_pluck(sfd_string* s, double amp_m, double pos) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (s->started) return fail(SFD_ESTATE, "pluck is an initial condition: excite before synthesizing");
+  if (!(pos > 0 && pos < 1) || !std::isfinite(amp_m)) return fail(SFD_EINVAL, "bad pluck");
+  s->exc = kPluck;
+  s->pluck_amp = amp_m;
+  s->pluck_pos = pos;
+  fill_desc(s);
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  return upload_initial(s);
+}
+
+sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, double pos, double omega_h,
+                             double alpha_h) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (s->started) return fail(SFD_ESTATE, "excite before synthesizing");
+  if (!(pos > 0 && pos < 1) || !(mass_kg > 0) || !(omega_h > 0) || !(alpha_h >= 1) || !std::isfinite(vel_mps))
+    return fail(SFD_EINVAL, "bad hammer parameters");
+  const sfd_string_params& p = s->p;
+  s->exc = kHammer;
+  fill_desc(s);
+  point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+  s->h.ham_M = static_cast<float>(mass_kg / (p.linear_density * p.length_m));
+  s->h.ham_k2w = static_cast<float>(s->k * s->k * std::pow(omega_h, 1.0 + alpha_h));
+  s->h.ham_expo = static_cast<float>(alpha_h - 1.0);
+  s->pluck_amp = 0;
+  s->hammer_uh1 = (vel_mps / p.length_m) * s->k;
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  return upload_initial(s);
+}
+
+sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double pos, double a_s_per_m, double eps,
+                          double release_time_s) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (s->started) return fail(SFD_ESTATE, "excite before synthesizing");
+  if (!(pos > 0 && pos < 1) || !(force_n >= 0) || !(eps >= 0 && eps <= 1) || !(a_s_per_m >= 0) ||
+      !std::isfinite(vel_mps))
+    return fail(SFD_EINVAL, "bad bow parameters");
+  const sfd_string_params& p = s->p;
+  s->exc = kBow;
+  s->pluck_amp = 0;
+  fill_desc(s);
+  point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+  s->h.bow_F = static_cast<float>(force_n / (p.linear_density * p.length_m * p.length_m));
+  s->h.bow_v = static_cast<float>(vel_mps / p.length_m);
+  s->h.bow_a = static_cast<float>(a_s_per_m * p.length_m);
+  s->h.bow_eps = static_cast<float>(eps);
+  if (release_time_s >= 0) {
+    // first step n with n k >= release (same comparison as stated in Eq. 5's use)
+    int64_t n = static_cast<int64_t>(std::ceil(release_time_s * p.fs));
+    while (n > 0 && static_cast<double>(n - 1) * s->k >= release_time_s) --n;
+    while (static_cast<double>(n) * s->k < release_time_s) ++n;
+    s->h.bow_release_n = n;
+  } else {
+    s->h.bow_release_n = INT64_MAX;
+  }
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  return upload_initial(s);
+}
+
+sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth, double phase_rad,
+                              double duration_s) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
+  Desc& D = s->h;
+  if (kind == SFD_MOD_NONE) {
+    D.mod_kind = 0;
+  } else if (kind == SFD_MOD_VIBRATO) {
+    if (!std::isfinite(rate_hz) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad vibrato");
+    if (std::pow(2.0, std::fabs(depth) / 1200.0) > s->p.f0_max_ratio * (1.0 + 1e-12))
+      return fail(SFD_EINVAL, "vibrato peak exceeds the grid's f0_max_ratio");
+    D.mod_kind = 1;
+    D.mod_inc = rate_hz * s->k;
+    D.mod_phase0 = phase_rad / (2.0 * kPi);
+    D.mod_depth2 = static_cast<float>(2.0 * depth / 1200.0);
+  } else if (kind == SFD_MOD_GLISS) {
+    if (!(duration_s > 0) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad glissando");
+    if (std::pow(2.0, std::max(0.0, depth)) > s->p.f0_max_ratio * (1.0 + 1e-12))
+      return fail(SFD_EINVAL, "glissando peak exceeds the grid's f0_max_ratio");
+    D.mod_kind = 2;
+    D.mod_inc = 2.0 * depth * s->k / duration_s;
+  } else {
+    return fail(SFD_EINVAL, "bad modulation kind");
+  }
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
+  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return SFD_OK;
+}
+
+sfd_status sfd_synthesize(sfd_string* s, int64_t n_samples, float* out, int32_t out_on_device) {
+  if (!s || (!out && n_samples > 0)) return fail(SFD_EINVAL, "NULL argument");
+  if (n_samples < 0) return fail(SFD_EINVAL, "n_samples < 0");
+  if (n_samples == 0) return SFD_OK;
+  sfd_ctx* c = s->ctx;
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  float* dout = out;
+  char* tmp = nullptr;
+  if (!out_on_device) {
+    tmp = c->pool.alloc(sizeof(float) * n_samples);
+    if (!tmp) return fail(SFD_ENOMEM, "device pool exhausted for the output buffer");
+    dout = reinterpret_cast<float*>(tmp);
+  }
+  std::vector<Job> jobs{Job{s->d_desc, dout, n_samples}};
+  std::vector<const sfd_string*> owners{s};
+  rc = launch_jobs(c, jobs, owners);
+  s->started = true;
+  if (rc == SFD_OK && !out_on_device) {
+    cudaError_t e = d2h(c, out, dout, sizeof(float) * n_samples);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy out");
+  }
+  Scalars sc{};
+  if (rc == SFD_OK) rc = read_status(s, &sc);
+  if (tmp) c->pool.dealloc(tmp);
+  if (rc) return rc;
+  rc = status_code(sc);
+  if (rc == SFD_EUNSTABLE) return fail(rc, "string state became non-finite");
+  if (rc == SFD_ENOCONV) return fail(rc, "coupled solve reached its sweep cap (result kept)");
+  return SFD_OK;
+}
+
+sfd_status sfd_string_position(const sfd_string* s, int64_t* time_level, int64_t* next_sample) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  Scalars sc{};
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  if ((rc = read_status(s, &sc))) return rc;
+  if (time_level) *time_level = sc.n;
+  if (next_sample) *next_sample = sc.next_out;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_state(const sfd_string* s, float* u_prev, float* u, float* z_prev, float* z) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  const Desc& D = s->h;
+  const int nz_full = s->n_l - 1;
+  std::vector<float> hu(D.n_u), hdu(D.n_u), hz(std::max(D.n_z, 1)), hdz(std::max(D.n_z, 1));
+  sfd_ctx* c = s->ctx;
+  SFD_CUDA(d2h(c, hu.data(), D.u, sizeof(float) * D.n_u));
+  SFD_CUDA(d2h(c, hdu.data(), D.du, sizeof(float) * D.n_u));
+  if (D.n_z > 0) {
+    SFD_CUDA(d2h(c, hz.data(), D.z, sizeof(float) * D.n_z));
+    SFD_CUDA(d2h(c, hdz.data(), D.dz, sizeof(float) * D.n_z));
+  }
+  SFD_CUDA(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < D.n_u; ++i) {
+    if (u) u[i] = hu[i];
+    if (u_prev) u_prev[i] = hu[i] - hdu[i];
+  }
+  for (int i = 0; i < nz_full; ++i) {
+    const float zv = D.n_z > 0 ? hz[i] : 0.f, dzv = D.n_z > 0 ? hdz[i] : 0.f;
+    if (z) z[i] = zv;
+    if (z_prev) z_prev[i] = zv - dzv;
+  }
+  return SFD_OK;
+}
+
+sfd_status sfd_string_stats(const sfd_string* s, int32_t* status, int32_t* max_sweeps, int64_t* total_sweeps) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  Scalars sc{};
+  if ((rc = read_status(s, &sc))) return rc;
+  if (status) *status = status_code(sc);
+  if (max_sweeps) *max_sweeps = sc.max_sweeps;
+  if (total_sweeps) *total_sweeps = sc.sweeps_total;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_destroy(sfd_string* s) {
+  if (!s) return SFD_OK;
+  if (s->batch_refs > 0) return fail(SFD_EBUSY, "string belongs to a live batch");
+  sfd_ctx* c = s->ctx;
+  if (set_device(c) == SFD_OK) cudaStreamSynchronize(c->stream);
+  c->pool.dealloc(s->block);
+  delete s;
+  return SFD_OK;
+}
+
+sfd_status sfd_batch_create(sfd_ctx* c, int32_t n, sfd_string* const* strings, sfd_batch** out) {
+  if (!c || !out || (n > 0 && !strings) || n < 0) return fail(SFD_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!strings[i] || strings[i]->ctx != c) return fail(SFD_EINVAL, "string %d is NULL or from another ctx", i);
+    for (int j = 0; j < i; ++j)
+      if (strings[j] == strings[i]) return fail(SFD_EINVAL, "string %d appears twice", i);
+  }
+  sfd_batch* b = new (std::nothrow) sfd_batch();
+  if (!b) return fail(SFD_ENOMEM, "host allocation failed");
+  b->ctx = c;
+  b->strings.assign(strings, strings + n);
+  for (auto* s : b->strings) s->batch_refs++;
+  *out = b;
+  return SFD_OK;
+}
+
+static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_device, const int64_t* offsets,
+                            int32_t* per_string_status) {
+  sfd_ctx* c = b->ctx;
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  std::vector<Job> jobs;
+  std::vector<const sfd_string*> owners;
+  for (size_t i = 0; i < b->strings.size(); ++i) {
+    if (n_samples[i] < 0) return fail(SFD_EINVAL, "n_samples[%zu] < 0", i);
+    if (n_samples[i] == 0) continue;
+    jobs.push_back(Job{b->strings[i]->d_desc, out_device + offsets[i], n_samples[i]});
+    owners.push_back(b->strings[i]);
+  }
+  rc = launch_jobs(c, jobs, owners);
+  for (auto* s : b->strings) s->started = true;
+  if (rc) return rc;
+  if (per_string_status) {
+    for (size_t i = 0; i < b->strings.size(); ++i) {
+      Scalars sc{};
+      if ((rc = read_status(b->strings[i], &sc))) return rc;
+      per_string_status[i] = status_code(sc);
+    }
+  }
+  return SFD_OK;
+}
+
+sfd_status sfd_batch_synthesize(sfd_batch* b, const int64_t* n_samples, float* out_device,
+                                const int64_t* out_offsets, int32_t* per_string_status) {
+  if (!b || !n_samples || !out_offsets || !out_device) return fail(SFD_EINVAL, "NULL argument");
+  return batch_run(b, n_samples, out_device, out_offsets, per_string_status);
+}
+
+sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, float* out_host,
+                                     const int64_t* out_offsets, int32_t* per_string_status) {
+  if (!b || !n_samples || !out_offsets || !out_host) return fail(SFD_EINVAL, "NULL argument");
+  sfd_ctx* c = b->ctx;
+  int64_t total = 0;
+  for (size_t i = 0; i < b->strings.size(); ++i) total = std::max(total, out_offsets[i] + n_samples[i]);
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  char* tmp = c->pool.alloc(sizeof(float) * std::max<int64_t>(total, 1));
+  if (!tmp) return fail(SFD_ENOMEM, "device pool exhausted for the output buffer");
+  float* dout = reinterpret_cast<float*>(tmp);
+  rc = batch_run(b, n_samples, dout, out_offsets, nullptr);
+  if (rc == SFD_OK) {
+    cudaError_t e = d2h(c, out_host, dout, sizeof(float) * total);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy out");
+    e = cudaStreamSynchronize(c->stream);
+    if (rc == SFD_OK && e != cudaSuccess) rc = cuda_fail(e, "sync");
+  }
+  if (rc == SFD_OK && per_string_status) {
+    for (size_t i = 0; i < b->strings.size(); ++i) {
+      Scalars sc{};
+      if ((rc = read_status(b->strings[i], &sc))) break;
+      per_string_status[i] = status_code(sc);
+    }
+  }
+  c->pool.dealloc(tmp);
+  return rc;
+}
+
+sfd_status sfd_batch_destroy(sfd_batch* b) {
+  if (!b) return SFD_OK;
+  for (auto* s : b->strings) s->batch_refs--;
+  delete b;
+  return SFD_OK;
+}
+
+}  // extern "C"

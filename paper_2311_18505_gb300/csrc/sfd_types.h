@@ -1,0 +1,91 @@
+// Internal layout shared by the host runtime (sfd_api.cu) and the step
+// kernel (sfd_kernel.cu).  All coefficients are computed on the host in
+// FP64 from the string parameters and rounded once to FP32.
+#pragma once
+
+#include <stdint.h>
+
+namespace sfd {
+
+constexpr int kWarp = 32;
+constexpr int kMaxSweeps = 24;       // cap of the coupled block Gauss-Seidel solve
+constexpr float kSweepTol = 5e-7f;   // relative change that ends the solve
+
+enum ExcKind : int32_t { kPluck = 0, kHammer = 1, kBow = 2 };
+enum StatusBits : int32_t { kStUnstable = 1, kStNoConv = 2 };
+
+// Per-string mutable scalars (device memory).
+struct Scalars {
+  float uh, duh;          // hammer u_H^n and u_H^n - u_H^{n-1} (normalised)
+  int64_t n;              // time level (state holds w^{n-1}, w^n)
+  int64_t next_out;       // index of the next output sample
+  int32_t status;         // StatusBits
+  int32_t max_sweeps;     // largest sweep count seen (diagnostic)
+  int64_t sweeps_total;   // total coupled-solve sweeps (diagnostic)
+};
+
+// Per-string descriptor (device memory, read-only in the kernel).
+struct Desc {
+  // grid: N_t, N_l intervals; n_u = N_t - 1, n_z = N_l - 1 unknowns;
+  // m_u, m_z rows per lane (odd, 32 m >= n + 1; m_z = 0 without z).
+  int32_t n_t, n_l, n_u, n_z, m_u, m_z;
+  int32_t boundary;       // 0 clamped, 1 simply supported
+  int32_t exc;            // ExcKind
+  int32_t linear;         // alpha == 1: z stays zero, matrix constant
+  int32_t mod_kind;       // 0 none, 1 vibrato, 2 glissando
+  int32_t z_jacobi;       // longitudinal off-diagonal folded into the sweeps
+  int32_t pad0_;
+  // delta-form coefficients (k^2-scaled Eq. 4), see the kernel
+  float th, tho;          // theta, (1 - theta)/2
+  float s0, s1, s1l;      // sigma0 k, sigma1 k / h_t^2, sigma1 k / h_l^2
+  float lam2, mu2, lam2l; // g^2 k^2 / h_t^2, kappa^2 k^2 / h_t^4, g^2 alpha^2 k^2 / h_l^2
+  float ca, cb, cz;       // phi' k^2 / (2 h_t^4), phi' k^2 / (2 h_t^3), phi' k^2 / (2 h_t^2 h_l)
+  float out_scale;        // L (output in metres)
+  int32_t o_node;         // pickup: nodes o_node, o_node + 1 (0..N_t)
+  float o_w;              //   weight of o_node + 1
+  int32_t e_node;         // excitation point, same convention
+  float e_w;
+  float jscale;           // J = I / h_t
+  // hammer (Eq. 6)
+  float ham_M;            // mass ratio M
+  float ham_k2w;          // k^2 omega_H^{1 + alpha_H}
+  float ham_expo;         // alpha_H - 1
+  // bow (Eq. 5)
+  float bow_F;            // F_B / (rho A L^2)
+  float bow_v;            // v_B / L
+  float bow_a;            // a L
+  float bow_eps;
+  float k;                // time step
+  float k2;               // k^2
+  int64_t bow_release_n;  // first step index with F_B = 0 (INT64_MAX: never)
+  // modulation: factor (gamma^n / gamma)^2 per step
+  double mod_inc;         // vibrato: rate k (cycles per step); gliss: 2 D k / T
+  double mod_phase0;      // vibrato: phase / (2 pi)
+  float mod_depth2;       // vibrato: 2 c / 1200
+  float pad_;
+  // state (device pointers into the string's pool block)
+  float* u;               // u^n            [n_u]
+  float* du;              // u^n - u^{n-1}  [n_u]
+  float* z;               // z^n            [n_z]
+  float* dz;              // z^n - z^{n-1}  [n_z]
+  float* xz;              // z-part of the unit-force response (warm start) [n_z]
+  float* az;              // last longitudinal acceleration (warm start) [n_z]
+  Scalars* sc;
+};
+
+// One unit of work for the persistent kernel.
+struct Job {
+  const Desc* desc;
+  float* out;             // first output sample of this job
+  int64_t n_samples;
+};
+
+// Shared-memory words one warp needs for a string with row counts m_u, m_z.
+constexpr int kArraysU = 19;
+constexpr int kArraysZ = 15;
+inline __host__ __device__ int warp_smem_floats(int m_u, int m_z) {
+  const int ru = kWarp * m_u + 4, rz = m_z > 0 ? kWarp * m_z + 4 : 0;
+  return kArraysU * ru + kArraysZ * rz;
+}
+
+}  // namespace sfd

@@ -1,0 +1,299 @@
+"""Python binding of the C-ABI in include/sfd.h (ctypes).
+
+Argument marshalling only: every step of the time-stepping runs in the CUDA
+library ``_build/libsfd.so``.  There is no CPU fallback; importing this
+module raises if the library has not been built.
+
+The functions keep the C names.  ``string_from_dict`` marshals a parameter
+dictionary (see ``workloads``) into create / excite / modulation calls.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfd.so")
+
+SFD_OK, SFD_EINVAL, SFD_ENOMEM, SFD_EUNSTABLE, SFD_ENOCONV = 0, -1, -2, -3, -4
+SFD_ECUDA, SFD_ETIMEOUT, SFD_EBUSY, SFD_ESTATE = -5, -6, -7, -8
+STATUS_NAMES = {0: "SFD_OK", -1: "SFD_EINVAL", -2: "SFD_ENOMEM", -3: "SFD_EUNSTABLE", -4: "SFD_ENOCONV",
+                -5: "SFD_ECUDA", -6: "SFD_ETIMEOUT", -7: "SFD_EBUSY", -8: "SFD_ESTATE"}
+SFD_MOD_NONE, SFD_MOD_VIBRATO, SFD_MOD_GLISS = 0, 1, 2
+
+
+class SfdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sfd_string_params(ctypes.Structure):
+    _fields_ = [
+        ("f0", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("sigma0", ctypes.c_double), ("sigma1", ctypes.c_double),
+        ("length_m", ctypes.c_double), ("fs", ctypes.c_double), ("linear_density", ctypes.c_double),
+        ("theta", ctypes.c_double), ("boundary", ctypes.c_int32), ("grid_rule", ctypes.c_int32),
+        ("pickup_pos", ctypes.c_double), ("f0_max_ratio", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsfd.so; raise if it is missing (the CUDA path is mandatory)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2311_18505_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "sfd_params_default": (None, [P(sfd_string_params)]),
+        "sfd_ctx_create": (i32, [ctypes.c_int, vp, ctypes.c_size_t, P(vp)]),
+        "sfd_ctx_destroy": (None, [vp]),
+        "sfd_ctx_memory": (i32, [vp, P(ctypes.c_size_t), P(ctypes.c_size_t)]),
+        "sfd_string_create": (i32, [vp, P(sfd_string_params), P(vp)]),
+        "sfd_string_info": (i32, [vp, P(i32), P(i32), P(dbl), P(dbl)]),
+        "sfd_excite_pluck": (i32, [vp, dbl, dbl]),
+        "sfd_excite_hammer": (i32, [vp, dbl, dbl, dbl, dbl, dbl]),
+        "sfd_excite_bow": (i32, [vp, dbl, dbl, dbl, dbl, dbl, dbl]),
+        "sfd_set_modulation": (i32, [vp, i32, dbl, dbl, dbl, dbl]),
+        "sfd_synthesize": (i32, [vp, i64, vp, i32]),
+        "sfd_string_position": (i32, [vp, P(i64), P(i64)]),
+        "sfd_string_state": (i32, [vp, vp, vp, vp, vp]),
+        "sfd_string_destroy": (i32, [vp]),
+        "sfd_string_stats": (i32, [vp, P(i32), P(i32), P(i64)]),
+        "sfd_batch_create": (i32, [vp, i32, P(vp), P(vp)]),
+        "sfd_batch_synthesize": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
+        "sfd_batch_synthesize_host": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
+        "sfd_batch_destroy": (i32, [vp]),
+        "sfd_last_launch_count": (i32, [vp]),
+        "sfd_ctx_transfer_bytes": (i32, [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "sfd_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()) -> int:
+    if rc != SFD_OK and rc not in allow:
+        raise SfdError(rc, lib().sfd_last_error().decode(errors="replace"))
+    return rc
+
+
+def _i64p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+# ---------------------------------------------------------------- C names
+
+def sfd_params_default() -> sfd_string_params:
+    p = sfd_string_params()
+    lib().sfd_params_default(ctypes.byref(p))
+    return p
+
+
+def sfd_ctx_create(device: int = 0, stream: int | None = None, mem_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfd_ctx_create(device, stream, mem_budget_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def sfd_ctx_destroy(ctx: int) -> None:
+    lib().sfd_ctx_destroy(ctx)
+
+
+def sfd_ctx_memory(ctx: int) -> tuple[int, int]:
+    u, t = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().sfd_ctx_memory(ctx, ctypes.byref(u), ctypes.byref(t)))
+    return u.value, t.value
+
+
+def sfd_string_create(ctx: int, params: sfd_string_params) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfd_string_create(ctx, ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def sfd_string_info(s: int) -> tuple[int, int, float, float]:
+    nt, nl, ht, hl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sfd_string_info(s, ctypes.byref(nt), ctypes.byref(nl), ctypes.byref(ht), ctypes.byref(hl)))
+    return nt.value, nl.value, ht.value, hl.value
+
+
+def sfd_excite_pluck(s: int, amp_m: float, pos: float) -> None:
+    _check(lib().sfd_excite_pluck(s, amp_m, pos))
+
+
+def sfd_excite_hammer(s: int, mass_kg: float, vel_mps: float, pos: float, omega_h: float = 3000.0,
+                      alpha_h: float = 2.5) -> None:
+    _check(lib().sfd_excite_hammer(s, mass_kg, vel_mps, pos, omega_h, alpha_h))
+
+
+def sfd_excite_bow(s: int, vel_mps: float, force_n: float, pos: float, a_s_per_m: float = 100.0,
+                   eps: float = 0.1, release_time_s: float = -1.0) -> None:
+    _check(lib().sfd_excite_bow(s, vel_mps, force_n, pos, a_s_per_m, eps, release_time_s))
+
+
+def sfd_set_modulation(s: int, kind: int, rate_hz: float = 0.0, depth: float = 0.0, phase_rad: float = 0.0,
+                       duration_s: float = 0.0) -> None:
+    _check(lib().sfd_set_modulation(s, kind, rate_hz, depth, phase_rad, duration_s))
+
+
+def sfd_synthesize(s: int, n_samples: int, out=None, allow_noconv: bool = False):
+    """Next n_samples samples.  `out` may be None (a NumPy array is returned),
+    a float32 NumPy array (host) or a CUDA float32 torch tensor (device)."""
+    allow = (SFD_ENOCONV,) if allow_noconv else ()
+    if out is None:
+        out = np.zeros(n_samples, dtype=np.float32)
+    if isinstance(out, np.ndarray):
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size >= n_samples
+        _check(lib().sfd_synthesize(s, n_samples, out.ctypes.data, 0), allow)
+    else:
+        assert out.is_cuda and out.dtype.is_floating_point and out.element_size() == 4 and out.is_contiguous()
+        _check(lib().sfd_synthesize(s, n_samples, out.data_ptr(), 1), allow)
+    return out
+
+
+def sfd_string_position(s: int) -> tuple[int, int]:
+    n, j = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sfd_string_position(s, ctypes.byref(n), ctypes.byref(j)))
+    return n.value, j.value
+
+
+def sfd_string_state(s: int):
+    nt, nl, _, _ = sfd_string_info(s)
+    up = np.zeros(nt - 1, np.float32); u = np.zeros(nt - 1, np.float32)
+    zp = np.zeros(max(nl - 1, 1), np.float32); z = np.zeros(max(nl - 1, 1), np.float32)
+    _check(lib().sfd_string_state(s, up.ctypes.data, u.ctypes.data, zp.ctypes.data, z.ctypes.data))
+    return up, u, zp[: nl - 1], z[: nl - 1]
+
+
+def sfd_string_stats(s: int) -> tuple[int, int, int]:
+    """(status, max sweeps, total sweeps) of the coupled solve."""
+    st, mx, tot = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().sfd_string_stats(s, ctypes.byref(st), ctypes.byref(mx), ctypes.byref(tot)))
+    return st.value, mx.value, tot.value
+
+
+def sfd_string_destroy(s: int) -> None:
+    _check(lib().sfd_string_destroy(s))
+
+
+def sfd_batch_create(ctx: int, strings) -> int:
+    arr = (ctypes.c_void_p * len(strings))(*strings)
+    h = ctypes.c_void_p()
+    _check(lib().sfd_batch_create(ctx, len(strings), arr, ctypes.byref(h)))
+    return h.value
+
+
+def sfd_batch_synthesize(b: int, n_samples, out_device, out_offsets, per_string_status: bool = False,
+                         allow_noconv: bool = False):
+    """Device output (CUDA torch tensor or raw pointer); asynchronous on the
+    context's stream unless per_string_status is requested."""
+    ns = np.ascontiguousarray(n_samples, dtype=np.int64)
+    offs = np.ascontiguousarray(out_offsets, dtype=np.int64)
+    ptr = out_device if isinstance(out_device, int) else out_device.data_ptr()
+    st = np.zeros(len(ns), dtype=np.int32) if per_string_status else None
+    stp = st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if st is not None else None
+    _check(lib().sfd_batch_synthesize(b, _i64p(ns), ptr, _i64p(offs), stp))
+    if st is not None:
+        bad = [int(x) for x in st if x != SFD_OK and not (allow_noconv and x == SFD_ENOCONV)]
+        if bad:
+            raise SfdError(bad[0], f"{len(bad)} string(s) reported {STATUS_NAMES.get(bad[0])}")
+    return st
+
+
+def sfd_batch_synthesize_host(b: int, n_samples, out_offsets=None, allow_noconv: bool = False):
+    ns = np.ascontiguousarray(n_samples, dtype=np.int64)
+    if out_offsets is None:
+        offs = np.zeros(len(ns), dtype=np.int64)
+        offs[1:] = np.cumsum(ns)[:-1]
+    else:
+        offs = np.ascontiguousarray(out_offsets, dtype=np.int64)
+    total = int((offs + ns).max()) if len(ns) else 0
+    out = np.zeros(max(total, 1), dtype=np.float32)
+    st = np.zeros(len(ns), dtype=np.int32)
+    _check(lib().sfd_batch_synthesize_host(b, _i64p(ns), out.ctypes.data, _i64p(offs),
+                                           st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    bad = [int(x) for x in st if x != SFD_OK and not (allow_noconv and x == SFD_ENOCONV)]
+    if bad:
+        raise SfdError(bad[0], f"{len(bad)} string(s) reported {STATUS_NAMES.get(bad[0])}")
+    return [out[o:o + n] for o, n in zip(offs, ns)], st
+
+
+def sfd_batch_destroy(b: int) -> None:
+    _check(lib().sfd_batch_destroy(b))
+
+
+def sfd_last_launch_count(ctx: int) -> int:
+    return lib().sfd_last_launch_count(ctx)
+
+
+def sfd_ctx_transfer_bytes(ctx: int) -> tuple[int, int]:
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().sfd_ctx_transfer_bytes(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def sfd_last_error() -> str:
+    return lib().sfd_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------ dict marshalling
+
+def params_from_dict(d: dict) -> sfd_string_params:
+    p = sfd_params_default()
+    if d.get("gamma"):
+        p.gamma = d["gamma"]
+    else:
+        p.f0 = d["f0"]
+    p.kappa, p.alpha, p.sigma0, p.sigma1 = d["kappa"], d["alpha"], d["sigma0"], d["sigma1"]
+    p.length_m = d.get("length", 1.0)
+    p.fs = d.get("fs", 48000.0)
+    p.linear_density = d.get("rho_a", 5e-3)
+    p.theta = d.get("theta", 0.5 * (1 + 4 / math.pi ** 2))
+    p.boundary = d.get("boundary", 0)
+    p.grid_rule = d.get("grid_rule", 0)
+    p.pickup_pos = d.get("pickup", 0.7)
+    mod = d.get("modulation", {"kind": "none"})
+    ratio = 1.0
+    if mod.get("kind") == "vibrato":
+        ratio = 2.0 ** (abs(mod["depth"]) / 1200.0)
+    elif mod.get("kind") == "gliss":
+        ratio = 2.0 ** max(0.0, mod["depth"])
+    p.f0_max_ratio = d.get("gamma_max_ratio", ratio)
+    return p
+
+
+def string_from_dict(ctx: int, d: dict) -> int:
+    s = sfd_string_create(ctx, params_from_dict(d))
+    try:
+        ex = d["excitation"]
+        if ex["kind"] == "pluck":
+            sfd_excite_pluck(s, ex["amp"], ex["pos"])
+        elif ex["kind"] == "hammer":
+            sfd_excite_hammer(s, ex["mass"], ex["vel"], ex["pos"], ex.get("omega", 3000.0), ex.get("alpha", 2.5))
+        else:
+            sfd_excite_bow(s, ex["vel"], ex["force"], ex["pos"], ex.get("a", 100.0), ex.get("eps", 0.1),
+                           ex.get("release", -1.0))
+        mod = d.get("modulation", {"kind": "none"})
+        if mod.get("kind") == "vibrato":
+            sfd_set_modulation(s, SFD_MOD_VIBRATO, mod["rate"], mod["depth"], mod.get("phase", 0.0), 0.0)
+        elif mod.get("kind") == "gliss":
+            sfd_set_modulation(s, SFD_MOD_GLISS, 0.0, mod["depth"], 0.0, mod["duration"])
+    except Exception:
+        sfd_string_destroy(s)
+        raise
+    return s

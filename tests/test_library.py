@@ -1,0 +1,69 @@
+"""Host-side checks of the C-ABI library (no GPU compute): it builds for
+sm_103a, loads, exports every function include/sfd.h declares, and reports
+a CUDA error (rather than falling back to the CPU) when no GPU is present."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import torch
+
+from paper_2311_18505_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "sfd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(sfd_[a-z_0-9]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("sfd_ctx_create", "sfd_string_create", "sfd_excite_pluck", "sfd_excite_hammer",
+                 "sfd_excite_bow", "sfd_synthesize", "sfd_string_destroy", "sfd_batch_create",
+                 "sfd_batch_synthesize", "sfd_batch_destroy", "sfd_last_error"):
+        assert must in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    L = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} declared in sfd.h but not exported"
+
+
+def test_binding_loads_and_defaults():
+    from paper_2311_18505_gb300 import sfd
+    p = sfd.sfd_params_default()
+    assert p.f0 == 110.0 and p.fs == 48000.0 and p.pickup_pos == 0.7
+    assert abs(p.theta - 0.5 * (1 + 4 / 3.141592653589793 ** 2)) < 1e-15
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU error path")
+def test_no_gpu_is_an_error_not_a_fallback():
+    from paper_2311_18505_gb300 import sfd
+    with pytest.raises(sfd.SfdError) as ei:
+        sfd.sfd_ctx_create(0, None, 1 << 20)
+    assert ei.value.code == sfd.SFD_ECUDA
+
+
+def test_binding_refuses_missing_library(tmp_path, monkeypatch):
+    from paper_2311_18505_gb300 import sfd
+    monkeypatch.setattr(sfd, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(sfd, "_lib", None)
+    with pytest.raises(ImportError):
+        sfd.lib()
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2311_18505_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "sfd_oracle" not in txt, f
