@@ -18,8 +18,13 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsfd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["sfd_kernel.cu", "sfd_api.cu"]
-HEADERS = ["sfd_types.h"]
+# (source, object, extra flags): the step kernel is compiled once per
+# transverse rows-per-lane class so each kernel gets its own register budget
+UNITS = [("sfd_api.cu", "sfd_api.o", [])] + \
+        [("sfd_kernel.cu", f"sfd_kernel_r{mu}.o", [f"-DSFD_MU={mu}"]) for mu in (1, 3, 5, 7, 9)] + \
+        [("sfd_kernel.cu", "sfd_kernel_smem.o", [])]
+SOURCES = sorted({u[0] for u in UNITS})
+HEADERS = ["sfd_types.h", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh"]
 
 
 def nvcc() -> str:
@@ -44,10 +49,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
     procs, objs = [], []
-    for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+    for src, o, extra in UNITS:
+        obj = os.path.join(OUT_DIR, o)
         objs.append(obj)
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -18,8 +18,16 @@
 #include "sfd_types.h"
 
 namespace sfd {
-cudaError_t launch_synth(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta,
-                         int n_ctas, cudaStream_t stream);
+#define SFD_DECLARE_LAUNCHER(name)                                                                   \
+  cudaError_t name(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta, \
+                   int n_ctas, cudaStream_t stream);
+SFD_DECLARE_LAUNCHER(launch_synth_reg1)
+SFD_DECLARE_LAUNCHER(launch_synth_reg3)
+SFD_DECLARE_LAUNCHER(launch_synth_reg5)
+SFD_DECLARE_LAUNCHER(launch_synth_reg7)
+SFD_DECLARE_LAUNCHER(launch_synth_reg9)
+SFD_DECLARE_LAUNCHER(launch_synth_smem)
+#undef SFD_DECLARE_LAUNCHER
 }
 
 using namespace sfd;
@@ -115,15 +123,19 @@ class Pool {
 
 }  // namespace
 
+constexpr int kClasses = 6;   // rows per lane 1, 3, 5, 7, 9 (registers), larger (shared memory)
+
 struct sfd_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side[kClasses] = {};      // one per kernel class, forked from `stream`
+  cudaEvent_t fork = nullptr, join[kClasses] = {};
   Pool pool;
   int sm_count = 0;
   size_t smem_optin = 0;
   Job* d_jobs = nullptr;
   int job_cap = 0;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;                // kClasses work-queue counters
   int last_launches = 0;
   uint64_t h2d_bytes = 0, d2h_bytes = 0;   // all host<->device copies made
 };
@@ -336,45 +348,80 @@ double job_cost(const sfd_string* s, int64_t n) {
   return per * static_cast<double>(n);
 }
 
-// Queue one launch of the persistent kernel over `jobs` (host array).
+int job_class(const Desc& D) {
+  if (D.m_u <= kMaxRegRows && (D.m_u & 1)) return D.m_u / 2;
+  return kClasses - 1;
+}
+
+using Launcher = cudaError_t (*)(const Job*, int, int*, int, int, int, cudaStream_t);
+const Launcher kLaunch[kClasses] = {launch_synth_reg1, launch_synth_reg3, launch_synth_reg5,
+                                    launch_synth_reg7, launch_synth_reg9, launch_synth_smem};
+
+// Queue the persistent kernels for `jobs` on the context stream: jobs are
+// grouped by kernel class (transverse rows per lane), each class sorted
+// longest first (the order its work queue hands them out), and the classes
+// run concurrently on side streams forked from and joined back to the
+// context stream.
 sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners) {
   c->last_launches = 0;
   if (jobs.empty()) return SFD_OK;
-  // longest jobs first: the work queue hands them out in this order
-  std::vector<int> order(jobs.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-  std::vector<double> cost(jobs.size());
-  int wf = 0;
-  for (size_t i = 0; i < jobs.size(); ++i) {
+  const int nj = static_cast<int>(jobs.size());
+  std::vector<int> order(nj), cls(nj);
+  std::vector<double> cost(nj);
+  for (int i = 0; i < nj; ++i) {
+    order[i] = i;
+    cls[i] = job_class(owners[i]->h);
     cost[i] = job_cost(owners[i], jobs[i].n_samples);
-    wf = std::max(wf, warp_smem_floats(owners[i]->h.m_u, owners[i]->h.m_z));
   }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  std::vector<Job> sorted(jobs.size());
-  for (size_t i = 0; i < jobs.size(); ++i) sorted[i] = jobs[order[i]];
-  sfd_status rc = ensure_jobs(c, static_cast<int>(sorted.size()));
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (cls[a] != cls[b]) return cls[a] < cls[b];
+    return cost[a] > cost[b];
+  });
+  std::vector<Job> sorted(nj);
+  int first[kClasses + 1] = {}, wf[kClasses] = {};
+  for (int i = 0; i < nj; ++i) sorted[i] = jobs[order[i]];
+  for (int i = 0; i < nj; ++i) {
+    const int k = cls[order[i]];
+    first[k + 1]++;
+    const Desc& D = owners[order[i]]->h;
+    wf[k] = std::max(wf[k], warp_smem_floats(D.m_u, D.m_z, D.z_jacobi));
+  }
+  for (int k = 0; k < kClasses; ++k) first[k + 1] += first[k];
+  sfd_status rc = ensure_jobs(c, nj);
   if (rc) return rc;
-  SFD_CUDA(h2d(c, c->d_jobs, sorted.data(), sizeof(Job) * sorted.size()));
-  const size_t wbytes = static_cast<size_t>(wf) * sizeof(float);
-  if (wbytes > c->smem_optin)
-    return fail(SFD_EINVAL, "string too large for one warp's shared memory (%zu > %zu bytes)", wbytes,
-                c->smem_optin);
-  const int n_jobs = static_cast<int>(sorted.size());
-  int wpc = static_cast<int>(std::min<size_t>(4, c->smem_optin / wbytes));
-  // spread warps over all SMs before stacking them
-  const int per_sm = (n_jobs + c->sm_count - 1) / c->sm_count;
-  wpc = std::max(1, std::min(wpc, per_sm));
+  SFD_CUDA(h2d(c, c->d_jobs, sorted.data(), sizeof(Job) * nj));
+  int active = 0;
+  for (int k = 0; k < kClasses; ++k) active += first[k + 1] > first[k];
+  // warps per CTA: one warp per job; stack warps only once every SM has some
+  int wpc_all = std::max(1, std::min(4, (nj + 2 * c->sm_count - 1) / (2 * c->sm_count)));
   if (const char* env = getenv("SFD_WARPS_PER_CTA")) {
-    int v = atoi(env);
-    if (v >= 1 && v <= 4 && static_cast<size_t>(v) * wbytes <= c->smem_optin) wpc = v;
+    const int v = atoi(env);
+    if (v >= 1 && v <= 4) wpc_all = v;
   }
-  const size_t cta_bytes = wbytes * wpc;
-  int ctas_per_sm = static_cast<int>(std::max<size_t>(1, (228u * 1024u) / (cta_bytes + 1024)));
-  ctas_per_sm = std::min(ctas_per_sm, 16);
-  int n_ctas = std::min((n_jobs + wpc - 1) / wpc, c->sm_count * ctas_per_sm);
-  cudaError_t e = launch_synth(c->d_jobs, n_jobs, c->d_counter, wf, wpc, n_ctas, c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "launch_synth");
-  c->last_launches = 1;
+  if (active > 1) SFD_CUDA(cudaEventRecord(c->fork, c->stream));
+  for (int k = 0; k < kClasses; ++k) {
+    const int n_k = first[k + 1] - first[k];
+    if (n_k == 0) continue;
+    const size_t wbytes = static_cast<size_t>(wf[k]) * sizeof(float);
+    if (wbytes > c->smem_optin)
+      return fail(SFD_EINVAL, "string too large for one warp's shared memory (%zu > %zu bytes)", wbytes,
+                  c->smem_optin);
+    int wpc = static_cast<int>(std::min<size_t>(static_cast<size_t>(wpc_all), c->smem_optin / wbytes));
+    wpc = std::max(1, wpc);
+    const int n_ctas = (n_k + wpc - 1) / wpc;
+    cudaStream_t st = c->stream;
+    if (active > 1) {
+      st = c->side[k];
+      SFD_CUDA(cudaStreamWaitEvent(st, c->fork, 0));
+    }
+    cudaError_t e = kLaunch[k](c->d_jobs + first[k], n_k, c->d_counter + k, wf[k], wpc, n_ctas, st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    c->last_launches++;
+    if (active > 1) {
+      SFD_CUDA(cudaEventRecord(c->join[k], st));
+      SFD_CUDA(cudaStreamWaitEvent(c->stream, c->join[k], 0));
+    }
+  }
   return SFD_OK;
 }
 
@@ -437,10 +484,19 @@ sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes
   c->smem_optin = prop.sharedMemPerBlockOptin;
   sfd_status rc = c->pool.init(mem_budget_bytes ? mem_budget_bytes : (size_t{256} << 20));
   if (rc) { delete c; return rc; }
-  if ((e = cudaMalloc(&c->d_counter, sizeof(int))) != cudaSuccess) {
+  if ((e = cudaMalloc(&c->d_counter, sizeof(int) * kClasses)) != cudaSuccess) {
     c->pool.release();
     delete c;
     return cuda_fail(e, "cudaMalloc(counter)");
+  }
+  bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < kClasses && ok; ++k) {
+    ok = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) {
+    sfd_ctx_destroy(c);
+    return fail(SFD_ECUDA, "stream/event creation failed");
   }
   *out = c;
   return SFD_OK;
@@ -450,6 +506,11 @@ void sfd_ctx_destroy(sfd_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < kClasses; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->join[k]) cudaEventDestroy(c->join[k]);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
   c->pool.release();
   if (c->d_jobs) cudaFree(c->d_jobs);
   if (c->d_counter) cudaFree(c->d_counter);
@@ -507,7 +568,7 @@ sfd_status sfd_string_create(sfd_ctx* c, const sfd_string_params* p, sfd_string*
   s->exc = kPluck;
   s->h.bow_release_n = INT64_MAX;
   fill_desc(s);
-  const size_t wbytes = static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z)) * sizeof(float);
+  const size_t wbytes = static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z, s->h.z_jacobi)) * sizeof(float);
   if (wbytes > c->smem_optin) {
     delete s;
     return fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", n_t, n_l);

@@ -1,0 +1,182 @@
+// Device helpers shared by the step kernels: warp tridiagonal partition
+// solver on shared-memory rows, reductions, point interpolation and the bow
+// friction root.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sfd_types.h"
+
+namespace sfd {
+
+#define SFD_FULL 0xffffffffu
+
+struct Red {           // per-lane factors of the reduced (lane-boundary) system
+  float k1[5], k2[5];
+  float binv, cl;
+};
+
+// ----------------------------------------------------------------------------
+// Tridiagonal partition solver on a warp.  Row i: a_i x_{i-1} + b_i x_i +
+// c_i x_{i+1} = d_i.  On entry SUB = a, INV = b, CP = c for the lane's rows;
+// on exit INV = 1/pivot, CP = c', AL = coefficient of the previous lane's last
+// unknown, FF/GG = back-substitution weights of the lane's last unknown and
+// the previous lane's last unknown.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void tri_factor(const float* __restrict__ SUB, float* __restrict__ INV,
+                                           float* __restrict__ CP, float* __restrict__ AL,
+                                           float* __restrict__ FF, float* __restrict__ GG, int m,
+                                           int lane, Red& rd) {
+  const int base = lane * m;
+  float cprev = 0.f, alprev = 0.f;
+  for (int r = 0; r < m; ++r) {
+    const int i = base + r;
+    const float a = SUB[i], b = INV[i], c = CP[i];
+    float inv, al;
+    if (r == 0) {
+      inv = 1.f / b;
+      al = a * inv;
+    } else {
+      inv = 1.f / (b - a * cprev);
+      al = -a * alprev * inv;
+    }
+    const float cp = c * inv;
+    INV[i] = inv;
+    CP[i] = cp;
+    AL[i] = al;
+    cprev = cp;
+    alprev = al;
+  }
+  float f = 1.f, g = 0.f;
+  FF[base + m - 1] = 1.f;
+  GG[base + m - 1] = 0.f;
+  for (int r = m - 2; r >= 0; --r) {
+    const int i = base + r;
+    const float cp = CP[i];
+    f = -cp * f;
+    g = -AL[i] - cp * g;
+    FF[i] = f;
+    GG[i] = g;
+  }
+  float f0n = __shfl_down_sync(SFD_FULL, FF[base], 1);
+  float g0n = __shfl_down_sync(SFD_FULL, GG[base], 1);
+  if (lane == kWarp - 1) { f0n = 0.f; g0n = 0.f; }
+  const float cl = CP[base + m - 1];
+  float A = AL[base + m - 1];
+  float B = 1.f + cl * g0n;
+  float C = cl * f0n;
+  rd.cl = cl;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int s = 1 << l;
+    float Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
+    float Cm = __shfl_up_sync(SFD_FULL, C, s);
+    float Ap = __shfl_down_sync(SFD_FULL, A, s), Bp = __shfl_down_sync(SFD_FULL, B, s);
+    float Cp = __shfl_down_sync(SFD_FULL, C, s);
+    if (lane < s) { Am = 0.f; Bm = 1.f; Cm = 0.f; }
+    if (lane + s >= kWarp) { Ap = 0.f; Bp = 1.f; Cp = 0.f; }
+    const float k1 = A / Bm, k2 = C / Bp;
+    A = -Am * k1;
+    C = -Cp * k2;
+    B = B - Cm * k1 - Ap * k2;
+    rd.k1[l] = k1;
+    rd.k2[l] = k2;
+  }
+  rd.binv = 1.f / B;
+}
+
+// Solve in place: E holds d for the lane's rows on entry and x on exit.
+__device__ __forceinline__ void tri_solve(const float* __restrict__ SUB, const float* __restrict__ INV,
+                                          const float* __restrict__ CP, const float* __restrict__ FF,
+                                          const float* __restrict__ GG, float* __restrict__ E, int m,
+                                          int lane, const Red& rd) {
+  const int base = lane * m;
+  float dp = 0.f;
+  for (int r = 0; r < m; ++r) {
+    const int i = base + r;
+    const float v = (r == 0) ? E[i] : E[i] - SUB[i] * dp;
+    dp = v * INV[i];
+    E[i] = dp;
+  }
+  const float dlast = dp;
+  float e = 0.f;
+  E[base + m - 1] = 0.f;
+  for (int r = m - 2; r >= 0; --r) {
+    const int i = base + r;
+    e = E[i] - CP[i] * e;
+    E[i] = e;
+  }
+  float e0n = __shfl_down_sync(SFD_FULL, E[base], 1);
+  if (lane == kWarp - 1) e0n = 0.f;
+  float D = dlast - rd.cl * e0n;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int s = 1 << l;
+    float Dm = __shfl_up_sync(SFD_FULL, D, s);
+    float Dp = __shfl_down_sync(SFD_FULL, D, s);
+    if (lane < s) Dm = 0.f;
+    if (lane + s >= kWarp) Dp = 0.f;
+    D = D - rd.k1[l] * Dm - rd.k2[l] * Dp;
+  }
+  const float X = D * rd.binv;
+  float Xp = __shfl_up_sync(SFD_FULL, X, 1);
+  if (lane == 0) Xp = 0.f;
+  for (int r = 0; r < m; ++r) {
+    const int i = base + r;
+    E[i] = E[i] + FF[i] * X + GG[i] * Xp;
+  }
+}
+
+// Stopping rule of the coupled Gauss-Seidel solve, from the largest
+// relative change e of the latest sweep and e_prev of the one before:
+// converged when e is below the tolerance, when the change predicted for
+// the next sweep (e^2 / e_prev for a linear contraction) is, or when the
+// change has stopped shrinking at the FP32 noise floor.
+__device__ __forceinline__ bool sweep_converged(float e, float e_prev, int sweep) {
+  if (e <= kSweepTol) return true;
+  if (sweep >= 2 && e < e_prev && e * e <= kSweepTol * e_prev) return true;
+  if (sweep >= 3 && e >= 0.5f * e_prev && e <= 64.f * kSweepTol) return true;
+  return false;
+}
+
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+  // non-negative floats order like their bit patterns
+  return __uint_as_float(__reduce_max_sync(SFD_FULL, __float_as_uint(v)));
+}
+
+// Value of a transverse-node field at nodes `node` and `node + 1` with weight w
+// on the second (linear interpolation I(x), Sec. 3.3); rows are node - 1 and the
+// fixed ends read the zero guard cells.
+__device__ __forceinline__ float interp2(const float* __restrict__ A, int node, float w) {
+  return (1.f - w) * A[node - 1] + w * A[node];
+}
+
+// Bow friction: solve v + c phi(v) = b with phi(v) = sign(v)(eps + (1-eps)
+// e^{-a|v|}) (Sec. 3.3.1, Eq. 5).  Sticking (v = 0, phi = b/c) whenever
+// |b| <= c; otherwise the root of the convex g(w) = w + c phi(w) - |b| on
+// (0, |b|).  Newton from w = |b| (right of the root) decreases monotonically
+// for a convex increasing g, so it stops as soon as an iterate fails to
+// decrease (the root within FP32 rounding) or g, g' leave their signs.
+__device__ __forceinline__ float bow_phi(float b, float c, float a, float eps) {
+  if (!(c > 0.f)) {
+    const float w = fabsf(b);
+    return b == 0.f ? 0.f : copysignf(eps + (1.f - eps) * expf(-a * w), b);
+  }
+  if (fabsf(b) <= c) return b / c;
+  const float B = fabsf(b);
+  float w = B;
+  for (int it = 0; it < 32; ++it) {
+    const float ex = expf(-a * w);
+    const float g = w + c * (eps + (1.f - eps) * ex) - B;
+    const float dg = 1.f - c * (1.f - eps) * a * ex;
+    if (!(g > 0.f) || !(dg > 0.f)) break;
+    const float wn = fmaxf(w - g / dg, 0.f);
+    if (!(wn < w)) break;
+    w = wn;
+  }
+  return copysignf(eps + (1.f - eps) * expf(-a * w), b);
+}
+
+}  // namespace sfd

@@ -1,0 +1,657 @@
+// Register-resident transverse path of the step kernel (included by
+// sfd_kernel.cu).  Same scheme and stages as the shared-memory path
+// (acceleration form of Eq. 4, partitioned tridiagonal solve, block
+// Gauss-Seidel with the longitudinal grid, scalar hammer / bow
+// elimination); the MU transverse rows of each lane live in registers with
+// fully unrolled loops, neighbours come from shuffles, and only the grid
+// transfer arrays and the longitudinal field stay in shared memory.
+#pragma once
+
+#include "sfd_device.cuh"
+
+namespace sfd {
+
+// Row values of x at offsets -2..+2 around the lane's chunk:
+// e[0] = row base-2, e[1] = base-1, e[2 + r] = x[r], e[MU+2] = base+MU, e[MU+3].
+template <int MU>
+__device__ __forceinline__ void extend(const float (&x)[MU], float (&e)[MU + 4], int lane) {
+  float l1 = __shfl_up_sync(SFD_FULL, x[MU - 1], 1);
+  float r1 = __shfl_down_sync(SFD_FULL, x[0], 1);
+  float l2, r2;
+  if (MU >= 2) {
+    l2 = __shfl_up_sync(SFD_FULL, x[MU >= 2 ? MU - 2 : 0], 1);
+    r2 = __shfl_down_sync(SFD_FULL, x[MU >= 2 ? 1 : 0], 1);
+    if (lane == 0) l2 = 0.f;
+    if (lane == kWarp - 1) r2 = 0.f;
+  } else {
+    l2 = __shfl_up_sync(SFD_FULL, x[0], 2);
+    r2 = __shfl_down_sync(SFD_FULL, x[0], 2);
+    if (lane < 2) l2 = 0.f;
+    if (lane >= kWarp - 2) r2 = 0.f;
+  }
+  if (lane == 0) l1 = 0.f;
+  if (lane == kWarp - 1) r1 = 0.f;
+  e[0] = l2;
+  e[1] = l1;
+#pragma unroll
+  for (int r = 0; r < MU; ++r) e[r + 2] = x[r];
+  e[MU + 2] = r1;
+  e[MU + 3] = r2;
+}
+
+// Left/right neighbours only.
+template <int MU>
+__device__ __forceinline__ void extend1(const float (&x)[MU], float (&e)[MU + 2], int lane) {
+  float l1 = __shfl_up_sync(SFD_FULL, x[MU - 1], 1);
+  float r1 = __shfl_down_sync(SFD_FULL, x[0], 1);
+  if (lane == 0) l1 = 0.f;
+  if (lane == kWarp - 1) r1 = 0.f;
+  e[0] = l1;
+#pragma unroll
+  for (int r = 0; r < MU; ++r) e[r + 1] = x[r];
+  e[MU + 1] = r1;
+}
+
+// Value of row q (uniform across the warp); 0 outside [0, n_u).
+template <int MU>
+__device__ __forceinline__ float row_value(const float (&x)[MU], int q, int n_u) {
+  const int qq = (q < 0 || q >= n_u) ? 0 : q;
+  const int r = qq % MU, src = qq / MU;
+  float t = 0.f;
+#pragma unroll
+  for (int k = 0; k < MU; ++k)
+    if (k == r) t = x[k];
+  const float v = __shfl_sync(SFD_FULL, t, src);
+  return (q < 0 || q >= n_u) ? 0.f : v;
+}
+
+template <int MU>
+__device__ __forceinline__ float node_interp(const float (&x)[MU], int node, float w, int n_u) {
+  return (1.f - w) * row_value<MU>(x, node - 1, n_u) + w * row_value<MU>(x, node, n_u);
+}
+
+// Partition factorisation of the lane's MU rows (register version of
+// tri_factor): on entry iv = diagonal, cp = super-diagonal, sb = sub-diagonal;
+// on exit iv = 1/pivot, cp = c', ff/gg = back-substitution weights.
+template <int MU>
+__device__ __forceinline__ void tri_factor_r(const float (&sb)[MU], float (&iv)[MU], float (&cp)[MU],
+                                             float (&ff)[MU], float (&gg)[MU], int lane, Red& rd) {
+  float al[MU];
+  float cprev = 0.f, alprev = 0.f;
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    float inv;
+    if (r == 0) {
+      inv = __frcp_rn(iv[r]);
+      al[r] = sb[r] * inv;
+    } else {
+      inv = __frcp_rn(iv[r] - sb[r] * cprev);
+      al[r] = -sb[r] * alprev * inv;
+    }
+    cp[r] = cp[r] * inv;
+    iv[r] = inv;
+    cprev = cp[r];
+    alprev = al[r];
+  }
+  ff[MU - 1] = 1.f;
+  gg[MU - 1] = 0.f;
+#pragma unroll
+  for (int r = MU - 2; r >= 0; --r) {
+    ff[r] = -cp[r] * ff[r + 1];
+    gg[r] = -al[r] - cp[r] * gg[r + 1];
+  }
+  float f0n = __shfl_down_sync(SFD_FULL, ff[0], 1);
+  float g0n = __shfl_down_sync(SFD_FULL, gg[0], 1);
+  if (lane == kWarp - 1) { f0n = 0.f; g0n = 0.f; }
+  const float cl = cp[MU - 1];
+  float A = al[MU - 1], B = 1.f + cl * g0n, C = cl * f0n;
+  rd.cl = cl;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int s = 1 << l;
+    float Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
+    float Cm = __shfl_up_sync(SFD_FULL, C, s);
+    float Ap = __shfl_down_sync(SFD_FULL, A, s), Bp = __shfl_down_sync(SFD_FULL, B, s);
+    float Cp = __shfl_down_sync(SFD_FULL, C, s);
+    if (lane < s) { Am = 0.f; Bm = 1.f; Cm = 0.f; }
+    if (lane + s >= kWarp) { Ap = 0.f; Bp = 1.f; Cp = 0.f; }
+    const float k1 = A * __frcp_rn(Bm), k2 = C * __frcp_rn(Bp);
+    A = -Am * k1;
+    C = -Cp * k2;
+    B = B - Cm * k1 - Ap * k2;
+    rd.k1[l] = k1;
+    rd.k2[l] = k2;
+  }
+  rd.binv = __frcp_rn(B);
+}
+
+// Solve one (NR = 1) or two (NR = 2) right-hand sides in place, interleaved.
+template <int MU, int NR>
+__device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (&iv)[MU], const float (&cp)[MU],
+                                            const float (&ff)[MU], const float (&gg)[MU], float (&x1)[MU],
+                                            float (&x2)[MU], int lane, const Red& rd) {
+  float p1 = 0.f, p2 = 0.f;
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    if (r == 0) {
+      p1 = x1[r] * iv[r];
+      if (NR == 2) p2 = x2[r] * iv[r];
+    } else {
+      p1 = (x1[r] - sb[r] * p1) * iv[r];
+      if (NR == 2) p2 = (x2[r] - sb[r] * p2) * iv[r];
+    }
+    x1[r] = p1;
+    if (NR == 2) x2[r] = p2;
+  }
+  const float dl1 = p1, dl2 = p2;
+  x1[MU - 1] = 0.f;
+  if (NR == 2) x2[MU - 1] = 0.f;
+#pragma unroll
+  for (int r = MU - 2; r >= 0; --r) {
+    x1[r] = x1[r] - cp[r] * x1[r + 1];
+    if (NR == 2) x2[r] = x2[r] - cp[r] * x2[r + 1];
+  }
+  float e1 = __shfl_down_sync(SFD_FULL, x1[0], 1);
+  float e2 = NR == 2 ? __shfl_down_sync(SFD_FULL, x2[0], 1) : 0.f;
+  if (lane == kWarp - 1) { e1 = 0.f; e2 = 0.f; }
+  float D1 = dl1 - rd.cl * e1, D2 = dl2 - rd.cl * e2;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) {
+    const int s = 1 << l;
+    float m1 = __shfl_up_sync(SFD_FULL, D1, s), q1 = __shfl_down_sync(SFD_FULL, D1, s);
+    float m2 = 0.f, q2 = 0.f;
+    if (NR == 2) {
+      m2 = __shfl_up_sync(SFD_FULL, D2, s);
+      q2 = __shfl_down_sync(SFD_FULL, D2, s);
+    }
+    if (lane < s) { m1 = 0.f; m2 = 0.f; }
+    if (lane + s >= kWarp) { q1 = 0.f; q2 = 0.f; }
+    D1 = D1 - rd.k1[l] * m1 - rd.k2[l] * q1;
+    if (NR == 2) D2 = D2 - rd.k1[l] * m2 - rd.k2[l] * q2;
+  }
+  const float X1 = D1 * rd.binv, X2 = D2 * rd.binv;
+  float Xp1 = __shfl_up_sync(SFD_FULL, X1, 1);
+  float Xp2 = NR == 2 ? __shfl_up_sync(SFD_FULL, X2, 1) : 0.f;
+  if (lane == 0) { Xp1 = 0.f; Xp2 = 0.f; }
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    x1[r] = x1[r] + ff[r] * X1 + gg[r] * Xp1;
+    if (NR == 2) x2[r] = x2[r] + ff[r] * X2 + gg[r] * Xp2;
+  }
+}
+
+template <int MU>
+__device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane) {
+  const Desc* __restrict__ Dp = job.desc;
+  const int n_t = Dp->n_t, n_l = Dp->n_l, n_u = Dp->n_u, n_z = Dp->n_z;
+  const int m_z = Dp->m_z;
+  const bool has_z = m_z > 0;
+  const bool linear = Dp->linear != 0;
+  const bool zjac = Dp->z_jacobi != 0;
+  const int exc = Dp->exc;
+  const int RU = kWarp * MU + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
+  const float th = Dp->th, tho = Dp->tho, s0 = Dp->s0, s1 = Dp->s1, s1l = Dp->s1l;
+  const float lam2_0 = Dp->lam2, mu2 = Dp->mu2, lam2l_0 = Dp->lam2l;
+  const float ca_0 = Dp->ca, cb_0 = Dp->cb, cz_0 = Dp->cz;
+  const float bsgn = Dp->boundary == 1 ? -1.f : 1.f;
+  const int mod_kind = Dp->mod_kind;
+  const double mod_inc = Dp->mod_inc, mod_phase0 = Dp->mod_phase0;
+  const float mod_depth2 = Dp->mod_depth2;
+  const float ham_k2w = Dp->ham_k2w, ham_expo = Dp->ham_expo, ham_M = Dp->ham_M;
+  const float bow_F = Dp->bow_F, bow_v = Dp->bow_v, bow_a = Dp->bow_a, bow_eps = Dp->bow_eps;
+  const float kk = Dp->k, k2 = Dp->k2;
+  const int64_t bow_release_n = Dp->bow_release_n;
+
+  // ---- shared memory: transverse transfer arrays, then the longitudinal grid ----
+  float* p = wbase;
+  auto U_ = [&]() { float* a = p + 2; p += RU; return a; };
+  float *FV = U_(), *XFC = U_(), *TMWs = U_();
+  int* TMIs = reinterpret_cast<int*>(U_());
+  float *Z = nullptr, *DZ = nullptr, *AZ = nullptr, *XZ = nullptr, *RZ_ = nullptr, *E1Z = nullptr;
+  float *E2Z = nullptr, *E3Z = nullptr, *SUBZ = nullptr, *INVZ = nullptr, *CPZ = nullptr, *ALZ = nullptr;
+  float *FFZ = nullptr, *GGZ = nullptr;
+  int *ZLO = nullptr, *ZHI = nullptr;
+  float *ZW0 = nullptr, *ZW1 = nullptr, *ZMK = nullptr;
+  if (has_z) {
+    auto Z_ = [&]() { float* a = p + 2; p += RZ; return a; };
+    Z = Z_(); DZ = Z_(); AZ = Z_(); XZ = Z_(); RZ_ = Z_(); E1Z = Z_(); E2Z = Z_(); E3Z = Z_();
+    ZLO = reinterpret_cast<int*>(Z_());
+    ZHI = reinterpret_cast<int*>(Z_());
+    ZW0 = Z_(); ZW1 = Z_(); ZMK = Z_();
+    if (!zjac) {
+      SUBZ = Z_(); INVZ = Z_(); CPZ = Z_(); ALZ = Z_(); FFZ = Z_(); GGZ = Z_();
+    }
+  }
+  const int total = static_cast<int>(p - wbase);
+  for (int k = lane; k < total; k += kWarp) wbase[k] = 0.f;
+  __syncwarp();
+
+  // ---- registers: the lane's transverse rows i = lane*MU + r ----
+  const int ub = lane * MU;
+  float U[MU], DU[MU];
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    const int i = ub + r;
+    U[r] = i < n_u ? Dp->u[i] : 0.f;
+    DU[r] = i < n_u ? Dp->du[i] : 0.f;
+  }
+  for (int i = lane; i < n_z; i += kWarp) {
+    Z[i] = Dp->z[i]; DZ[i] = Dp->dz[i]; XZ[i] = Dp->xz[i]; AZ[i] = Dp->az[i];
+  }
+  Scalars* scp = Dp->sc;
+  int64_t n = scp->n, jnext = scp->next_out;
+  float uh = scp->uh, duh = scp->duh;
+  int status = scp->status;
+  int max_sweeps = scp->max_sweeps;
+  int64_t sweeps_total = scp->sweeps_total;
+
+  // grid transfer maps (exact integer positions)
+  if (has_z) {
+#pragma unroll
+    for (int r = 0; r < MU; ++r) {
+      const int i = ub + r;
+      if (i < n_u) {
+        const int pos = (i + 1) * n_l;
+        const int mm = pos / n_t;
+        TMIs[i] = mm;
+        TMWs[i] = static_cast<float>(pos - mm * n_t) / static_cast<float>(n_t);
+      }
+    }
+    // longitudinal row i (node mm = i + 1) gathers from transverse nodes
+    // [lo, hi]; when N_l >= N_t that range holds at most two nodes, whose
+    // hat weights are stored (w0 for lo, w1 for lo + 1).  Pad rows get an
+    // empty range, zero weights and a zero mask.
+    for (int i = lane; i < kWarp * m_z; i += kWarp) {
+      const int mm = i + 1;
+      int lo = ((mm - 1) * n_t) / n_l + 1;
+      int hi = ((mm + 1) * n_t + n_l - 1) / n_l - 1;
+      lo = lo < 1 ? 1 : lo;
+      hi = hi > n_t - 1 ? n_t - 1 : hi;
+      if (i >= n_z) { lo = 1; hi = 0; }
+      ZLO[i] = lo;
+      ZHI[i] = hi;
+      const int d0 = lo * n_l - mm * n_t, d1 = (lo + 1) * n_l - mm * n_t;
+      ZW0[i] = lo <= hi ? 1.f - static_cast<float>(d0 < 0 ? -d0 : d0) / static_cast<float>(n_t) : 0.f;
+      ZW1[i] = lo + 1 <= hi ? 1.f - static_cast<float>(d1 < 0 ? -d1 : d1) / static_cast<float>(n_t) : 0.f;
+      ZMK[i] = i < n_z ? 1.f : 0.f;
+    }
+  }
+  const bool two_slot = n_l >= n_t;
+  __syncwarp();
+  const float inv_nt = 1.f / static_cast<float>(n_t);
+  auto interp_z = [&](const float* A, int i) {
+    const int mm = TMIs[i];
+    const float w = TMWs[i];
+    return (1.f - w) * A[mm - 1] + w * A[mm];
+  };
+  auto spread = [&](const float* F, int i) {
+    const int lo = ZLO[i];
+    if (two_slot) return ZW0[i] * F[lo - 1] + ZW1[i] * F[lo];
+    const int mm = i + 1, hi = ZHI[i];
+    float acc = 0.f;
+    for (int l = lo; l <= hi; ++l) {
+      const int dd = l * n_l - mm * n_t;
+      const float w = 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt;
+      acc = fmaf(w, F[l - 1], acc);
+    }
+    return acc;
+  };
+
+  // ---- constant matrices ----
+  Red rdu, rdz;
+  const float dz_diag = 1.f + s0 + 2.f * s1l;
+  const float dz_inv = __frcp_rn(dz_diag);
+  if (has_z && !zjac) {
+    for (int r = 0; r < m_z; ++r) {
+      const int i = lane * m_z + r;
+      if (i < n_z) {
+        SUBZ[i] = i > 0 ? -s1l : 0.f;
+        INVZ[i] = dz_diag;
+        CPZ[i] = i < n_z - 1 ? -s1l : 0.f;
+      } else {
+        SUBZ[i] = 0.f; INVZ[i] = 1.f; CPZ[i] = 0.f;
+      }
+    }
+    tri_factor(SUBZ, INVZ, CPZ, ALZ, FFZ, GGZ, m_z, lane, rdz);
+  }
+  float SB[MU], IV[MU], CPr[MU], FFr[MU], GGr[MU];
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    const int i = ub + r;
+    if (i < n_u) {
+      SB[r] = i > 0 ? tho - s1 : 0.f;
+      IV[r] = th + s0 + 2.f * s1;
+      CPr[r] = i < n_u - 1 ? tho - s1 : 0.f;
+    } else {
+      SB[r] = 0.f; IV[r] = 1.f; CPr[r] = 0.f;
+    }
+  }
+  const bool forced = exc != kPluck;
+  const int en = Dp->e_node;
+  const float ew = Dp->e_w, js = Dp->jscale;
+  float XP[MU];
+  auto load_J = [&](float (&E)[MU]) {
+#pragma unroll
+    for (int r = 0; r < MU; ++r) {
+      const int i = ub + r;
+      float v = 0.f;
+      if (i == en - 1) v += (1.f - ew) * js;
+      if (i == en) v += ew * js;
+      E[r] = (i < n_u) ? v : 0.f;
+    }
+  };
+#pragma unroll
+  for (int r = 0; r < MU; ++r) XP[r] = 0.f;
+  if (linear) {
+    tri_factor_r<MU>(SB, IV, CPr, FFr, GGr, lane, rdu);
+    if (forced) {
+      load_J(XP);
+      tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, XP, XP, lane, rdu);
+    }
+  }
+  __syncwarp();
+
+  const int on = Dp->o_node;
+  const float ow = Dp->o_w, oscale = Dp->out_scale;
+  const int64_t j_end = jnext + job.n_samples;
+  float outbuf = 0.f;
+  int64_t opos = 0;
+  float AC[MU];
+
+  while (jnext < j_end) {
+    if (jnext > n && !(status & kStUnstable)) {
+      // ======================= one step n -> n+1 =======================
+      float rm = 1.f;
+      if (mod_kind == 1) {
+        double t = fma(static_cast<double>(n), mod_inc, mod_phase0);
+        t -= floor(t);
+        rm = exp2f(mod_depth2 * sinf(6.28318530717958647f * static_cast<float>(t)));
+      } else if (mod_kind == 2) {
+        rm = exp2f(static_cast<float>(mod_inc * static_cast<double>(n)));
+      }
+      const float lam2 = lam2_0 * rm, lam2l = lam2l_0 * rm;
+      const float ca = ca_0 * rm, cb = cb_0 * rm, cz = cz_0 * rm;
+
+      float eta = 0.f, k2G = 0.f, FB = 0.f;
+      if (exc == kHammer) {
+        eta = uh - node_interp<MU>(U, en, ew, n_u);
+        if (eta > 0.f) k2G = ham_k2w * powf(eta, ham_expo);
+      } else if (exc == kBow) {
+        FB = (n < bow_release_n) ? bow_F : 0.f;
+      }
+      const bool need_resp = !linear && ((exc == kHammer && k2G > 0.f) || (exc == kBow && FB > 0.f));
+
+      // ---- stage 1: transverse right-hand side and matrix (registers) ----
+      float Ue[MU + 4], DUe[MU + 2], GL[MU], GR[MU];
+      extend<MU>(U, Ue, lane);
+      extend1<MU>(DU, DUe, lane);
+#pragma unroll
+      for (int r = 0; r < MU; ++r) {
+        GL[r] = Ue[r + 2] - Ue[r + 1];
+        GR[r] = Ue[r + 3] - Ue[r + 2];
+      }
+      float ZTe[MU + 2];
+      if (has_z) {
+        float zt[MU];
+#pragma unroll
+        for (int r = 0; r < MU; ++r) zt[r] = (ub + r < n_u) ? interp_z(Z, ub + r) : 0.f;
+        extend1<MU>(zt, ZTe, lane);
+      }
+      float RA[MU];
+#pragma unroll
+      for (int r = 0; r < MU; ++r) {
+        const int i = ub + r;
+        const float u0 = Ue[r + 2], um1 = Ue[r + 1], up1 = Ue[r + 3], um2 = Ue[r], up2 = Ue[r + 4];
+        const float gl = GL[r], gr = GR[r];
+        const float d2 = gr - gl;
+        float d4 = ((up2 - up1) - gr) - 2.f * d2 + (gl - (um1 - um2));
+        if (i == 0) d4 += bsgn * u0;
+        if (i == n_u - 1) d4 += bsgn * u0;
+        const float du0 = DUe[r + 1];
+        const float d2du = (DUe[r + 2] - du0) - (du0 - DUe[r]);
+        float rhs = lam2 * d2 - mu2 * d4 - 2.f * s0 * du0 + 2.f * s1 * d2du;
+        if (!linear) {
+          const float gl2 = gl * gl, gr2 = gr * gr;
+          float yl = 2.f * ca * gl2 * gl, yr = 2.f * ca * gr2 * gr;
+          if (has_z) {
+            yl += 4.f * cb * gl * (ZTe[r + 1] - ZTe[r]);
+            yr += 4.f * cb * gr * (ZTe[r + 2] - ZTe[r + 1]);
+            if (i < n_u) FV[i] = gr2 - gl2;
+          }
+          rhs += yr - yl;
+          if (i < n_u) {
+            SB[r] = i > 0 ? tho - s1 - ca * gl2 : 0.f;
+            IV[r] = th + s0 + 2.f * s1 + ca * (gl2 + gr2);
+            CPr[r] = i < n_u - 1 ? tho - s1 - ca * gr2 : 0.f;
+          }
+        }
+        RA[r] = i < n_u ? rhs : 0.f;
+      }
+      if (!linear) tri_factor_r<MU>(SB, IV, CPr, FFr, GGr, lane, rdu);
+      __syncwarp();
+
+      if (!has_z) {
+#pragma unroll
+        for (int r = 0; r < MU; ++r) AC[r] = RA[r];
+        if (need_resp) {
+          load_J(XP);
+          tri_solve_r<MU, 2>(SB, IV, CPr, FFr, GGr, AC, XP, lane, rdu);
+        } else {
+          tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
+        }
+      } else {
+        // ---- stage 2: longitudinal right-hand side ----
+#pragma unroll 2
+        for (int k = 0; k < m_z; ++k) {
+          const int i = lane + kWarp * k;
+          const float z0 = Z[i];
+          const float d2z = (Z[i + 1] - z0) - (z0 - Z[i - 1]);
+          const float dz0 = DZ[i];
+          const float d2dz = (DZ[i + 1] - dz0) - (dz0 - DZ[i - 1]);
+          RZ_[i] = ZMK[i] * (lam2l * d2z - 2.f * s0 * dz0 + 2.f * s1l * d2dz + 2.f * cz * spread(FV, i));
+        }
+        __syncwarp();
+        // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
+        int sweep = 0;
+        float e_prev = 0.f;
+        for (;;) {
+          float az[MU], AZe[MU + 2];
+#pragma unroll
+          for (int r = 0; r < MU; ++r) az[r] = (ub + r < n_u) ? interp_z(AZ, ub + r) : 0.f;
+          extend1<MU>(az, AZe, lane);
+#pragma unroll
+          for (int r = 0; r < MU; ++r)
+            AC[r] = (ub + r < n_u) ? RA[r] + cb * (GR[r] * (AZe[r + 2] - AZe[r + 1]) - GL[r] * (AZe[r + 1] - AZe[r]))
+                                   : 0.f;
+          if (need_resp) {
+            float xz[MU], XZe[MU + 2];
+#pragma unroll
+            for (int r = 0; r < MU; ++r) xz[r] = (ub + r < n_u) ? interp_z(XZ, ub + r) : 0.f;
+            extend1<MU>(xz, XZe, lane);
+            load_J(XP);
+#pragma unroll
+            for (int r = 0; r < MU; ++r)
+              if (ub + r < n_u)
+                XP[r] += cb * (GR[r] * (XZe[r + 2] - XZe[r + 1]) - GL[r] * (XZe[r + 1] - XZe[r]));
+            tri_solve_r<MU, 2>(SB, IV, CPr, FFr, GGr, AC, XP, lane, rdu);
+          } else {
+            tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
+          }
+          // nodal d_+[g d(.)] of the new accelerations for the longitudinal rows
+          {
+            float ACe[MU + 2];
+            extend1<MU>(AC, ACe, lane);
+#pragma unroll
+            for (int r = 0; r < MU; ++r)
+              if (ub + r < n_u)
+                FV[ub + r] = GR[r] * (ACe[r + 2] - ACe[r + 1]) - GL[r] * (ACe[r + 1] - ACe[r]);
+            if (need_resp) {
+              float XPe[MU + 2];
+              extend1<MU>(XP, XPe, lane);
+#pragma unroll
+              for (int r = 0; r < MU; ++r)
+                if (ub + r < n_u)
+                  XFC[ub + r] = GR[r] * (XPe[r + 2] - XPe[r + 1]) - GL[r] * (XPe[r + 1] - XPe[r]);
+            }
+          }
+          __syncwarp();
+          float chg = 0.f, mag = 0.f, chx = 0.f, mgx = 0.f;
+          if (zjac) {
+            // one Jacobi update of each field into the spare buffer, then swap
+#pragma unroll 2
+            for (int k = 0; k < m_z; ++k) {
+              const int i = lane + kWarp * k;
+              const float mk = ZMK[i];
+              const float v = mk * (RZ_[i] + cz * spread(FV, i) + s1l * (AZ[i - 1] + AZ[i + 1])) * dz_inv;
+              chg = fmaxf(chg, fabsf(v - AZ[i]));
+              mag = fmaxf(mag, fmaxf(fabsf(v), fabsf(DZ[i])));
+              E2Z[i] = v;
+              if (need_resp) {
+                const float x = mk * (cz * spread(XFC, i) + s1l * (XZ[i - 1] + XZ[i + 1])) * dz_inv;
+                chx = fmaxf(chx, fabsf(x - XZ[i]));
+                mgx = fmaxf(mgx, fabsf(x));
+                E3Z[i] = x;
+              }
+            }
+            __syncwarp();
+            { float* t = AZ; AZ = E2Z; E2Z = t; }
+            if (need_resp) { float* t = XZ; XZ = E3Z; E3Z = t; }
+          } else {
+            for (int r = 0; r < m_z; ++r) {
+              const int i = lane * m_z + r;
+              E1Z[i] = i < n_z ? RZ_[i] + cz * spread(FV, i) : 0.f;
+            }
+            tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
+            for (int r = 0; r < m_z; ++r) {
+              const int i = lane * m_z + r;
+              const float v = E1Z[i];
+              chg = fmaxf(chg, fabsf(v - AZ[i]));
+              mag = fmaxf(mag, fmaxf(fabsf(v), fabsf(DZ[i])));
+              AZ[i] = v;
+            }
+            if (need_resp) {
+              for (int r = 0; r < m_z; ++r) {
+                const int i = lane * m_z + r;
+                E1Z[i] = i < n_z ? cz * spread(XFC, i) : 0.f;
+              }
+              tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
+              for (int r = 0; r < m_z; ++r) {
+                const int i = lane * m_z + r;
+                const float v = E1Z[i];
+                chx = fmaxf(chx, fabsf(v - XZ[i]));
+                mgx = fmaxf(mgx, fabsf(v));
+                XZ[i] = v;
+              }
+            }
+          }
+          chg = warp_max_nonneg(chg);
+          mag = warp_max_nonneg(mag);
+          chx = warp_max_nonneg(chx);
+          mgx = warp_max_nonneg(mgx);
+          __syncwarp();
+          ++sweep;
+          const float e = fmaxf(chg > 0.f ? chg / mag : 0.f, chx > 0.f ? chx / mgx : 0.f);
+          if (sweep_converged(e, e_prev, sweep)) break;
+          if (sweep >= kMaxSweeps) { status |= kStNoConv; break; }
+          e_prev = e;
+        }
+        sweeps_total += sweep;
+        if (sweep > max_sweeps) max_sweeps = sweep;
+      }
+
+      // ---- stage 4: excitation force (scalar elimination) ----
+      if (exc == kHammer) {
+        float s = 0.f;
+        if (k2G > 0.f) {
+          const float cm = 0.5f * ham_M * k2G;
+          s = cm * (2.f * eta - node_interp<MU>(AC, en, ew, n_u)) /
+              (1.f + 0.5f * k2G + cm * node_interp<MU>(XP, en, ew, n_u));
+          duh -= s / ham_M;
+        }
+        uh += duh;
+        if (s != 0.f) {
+#pragma unroll
+          for (int r = 0; r < MU; ++r) AC[r] = fmaf(s, XP[r], AC[r]);
+          if (has_z)
+            for (int k = 0; k < m_z; ++k) {
+              const int i = lane + kWarp * k;
+              AZ[i] = fmaf(s, XZ[i], AZ[i]);
+            }
+        }
+      } else if (exc == kBow && FB > 0.f) {
+        const float b = (node_interp<MU>(AC, en, ew, n_u) + 2.f * node_interp<MU>(DU, en, ew, n_u)) / (2.f * kk) -
+                        bow_v;
+        const float c = 0.5f * kk * FB * node_interp<MU>(XP, en, ew, n_u);
+        const float phi = bow_phi(b, c, bow_a, bow_eps);
+        const float s = -k2 * FB * phi;
+#pragma unroll
+        for (int r = 0; r < MU; ++r) AC[r] = fmaf(s, XP[r], AC[r]);
+        if (has_z)
+          for (int k = 0; k < m_z; ++k) {
+            const int i = lane + kWarp * k;
+            AZ[i] = fmaf(s, XZ[i], AZ[i]);
+          }
+      }
+
+      // ---- stage 5: advance the time level ----
+      bool bad = false;
+#pragma unroll
+      for (int r = 0; r < MU; ++r) {
+        if (ub + r < n_u) {
+          DU[r] = DU[r] + AC[r];
+          U[r] = U[r] + DU[r];
+          bad |= !isfinite(U[r]);
+        }
+      }
+      if (has_z) {
+        for (int k = 0; k < m_z; ++k) {
+          const int i = lane + kWarp * k;
+          const float d = DZ[i] + AZ[i];
+          DZ[i] = d;
+          Z[i] += d;
+        }
+      }
+      if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
+      __syncwarp();
+      ++n;
+    }
+    float y;
+    if (jnext == n - 1)
+      y = node_interp<MU>(U, on, ow, n_u) - node_interp<MU>(DU, on, ow, n_u);
+    else
+      y = node_interp<MU>(U, on, ow, n_u);
+    y *= oscale;
+    if (status & kStUnstable) y = 0.f;
+    if ((opos & (kWarp - 1)) == lane) outbuf = y;
+    ++opos;
+    if ((opos & (kWarp - 1)) == 0) job.out[opos - kWarp + lane] = outbuf;
+    ++jnext;
+  }
+  {
+    const int rem = static_cast<int>(opos & (kWarp - 1));
+    if (lane < rem) job.out[opos - rem + lane] = outbuf;
+  }
+
+  // ---- store the state ----
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < MU; ++r) {
+    const int i = ub + r;
+    if (i < n_u) { Dp->u[i] = U[r]; Dp->du[i] = DU[r]; }
+  }
+  for (int i = lane; i < n_z; i += kWarp) {
+    Dp->z[i] = Z[i]; Dp->dz[i] = DZ[i]; Dp->xz[i] = XZ[i]; Dp->az[i] = AZ[i];
+  }
+  if (lane == 0) {
+    scp->n = n;
+    scp->next_out = jnext;
+    scp->uh = uh;
+    scp->duh = duh;
+    scp->status = status;
+    scp->max_sweeps = max_sweeps;
+    scp->sweeps_total = sweeps_total;
+  }
+  __syncwarp();
+}
+
+}  // namespace sfd

@@ -92,10 +92,25 @@ def test_bow_short_window(sfd, ctx, alpha):
     dict(f0=110.0, alpha=3.0, boundary=1),      # simply supported ends
     dict(f0=55.0, alpha=6.0, kappa=2.7, sigma0=2.0, sigma1=1e-4),
     dict(f0=110.0, alpha=1.0, kappa=0.0, theta=1.0),
+    dict(f0=55.0, alpha=2.0, kappa=0.0),        # N_t ~ 277: 9 transverse rows per lane
+    dict(f0=40.0, alpha=2.0, kappa=0.0),        # N_t ~ 382: shared-memory path
+    dict(f0=40.0, alpha=1.0, kappa=0.0),        # shared-memory path, linear
+    dict(f0=48000.0 / 6.0 / 3.14, alpha=1.5, kappa=0.0),   # N_t = 2-3: a single unknown
 ])
 def test_grid_edge_cases(sfd, ctx, case):
     d = W.make(excitation={"kind": "pluck", "amp": 2e-3, "pos": 0.37}, n_samples=6000, **case)
     assert rel_l2(gpu_run(sfd, ctx, d), oracle.run(d)) <= TOL
+
+
+@pytest.mark.parametrize("exc", [HAMMER, BOW])
+def test_forced_shared_memory_path(sfd, ctx, exc):
+    """Hammer and bow on a grid too large for the register path."""
+    d = W.make(f0=40.0, alpha=2.0, kappa=0.0, excitation=exc, n_samples=3000)
+    y, ref = gpu_run(sfd, ctx, d), oracle.run(d)
+    if exc["kind"] == "hammer":
+        assert rel_l2(y, ref) <= TOL
+    else:
+        assert rel_l2(y[:150], ref[:150]) <= 1e-3
 
 
 def test_grid_sizes_match_oracle(sfd, ctx):
