@@ -16,7 +16,25 @@ namespace sfd {
 struct Red {           // per-lane factors of the reduced (lane-boundary) system
   float k1[5], k2[5];
   float binv, cl;
+  int nlev;            // cyclic-reduction levels kept (warp-uniform)
 };
+
+// Reciprocal for the eliminations: one MUFU instruction (rcp.approx.ftz,
+// about 1 ulp) instead of the IEEE sequence with its slow-path branch.  The
+// pivots are O(1) (the systems are strictly diagonally dominant), so
+// flushing subnormals never applies; the solves then carry FP32-rounding
+// sized errors, which scale with the small accelerations being solved for.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Cyclic reduction stops once every lane's remaining off-diagonal coupling
+// is below this fraction of its diagonal: the reduced system is then
+// diagonal to FP32 precision (a strictly diagonally dominant tridiagonal
+// squares its coupling ratio at every level).
+constexpr float kPcrDrop = 7.4505806e-9f;   // 2^-27
 
 // ----------------------------------------------------------------------------
 // Tridiagonal partition solver on a warp.  Row i: a_i x_{i-1} + b_i x_i +
@@ -36,10 +54,10 @@ __device__ __forceinline__ void tri_factor(const float* __restrict__ SUB, float*
     const float a = SUB[i], b = INV[i], c = CP[i];
     float inv, al;
     if (r == 0) {
-      inv = 1.f / b;
+      inv = fast_rcp(b);
       al = a * inv;
     } else {
-      inv = 1.f / (b - a * cprev);
+      inv = fast_rcp(b - a * cprev);
       al = -a * alprev * inv;
     }
     const float cp = c * inv;
@@ -68,8 +86,12 @@ __device__ __forceinline__ void tri_factor(const float* __restrict__ SUB, float*
   float B = 1.f + cl * g0n;
   float C = cl * f0n;
   rd.cl = cl;
+  rd.nlev = 5;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) { rd.k1[l] = 0.f; rd.k2[l] = 0.f; }
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
+    if (__all_sync(SFD_FULL, fabsf(A) + fabsf(C) <= kPcrDrop * fabsf(B))) { rd.nlev = l; break; }
     const int s = 1 << l;
     float Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
     float Cm = __shfl_up_sync(SFD_FULL, C, s);
@@ -77,14 +99,14 @@ __device__ __forceinline__ void tri_factor(const float* __restrict__ SUB, float*
     float Cp = __shfl_down_sync(SFD_FULL, C, s);
     if (lane < s) { Am = 0.f; Bm = 1.f; Cm = 0.f; }
     if (lane + s >= kWarp) { Ap = 0.f; Bp = 1.f; Cp = 0.f; }
-    const float k1 = A / Bm, k2 = C / Bp;
+    const float k1 = A * fast_rcp(Bm), k2 = C * fast_rcp(Bp);
     A = -Am * k1;
     C = -Cp * k2;
     B = B - Cm * k1 - Ap * k2;
     rd.k1[l] = k1;
     rd.k2[l] = k2;
   }
-  rd.binv = 1.f / B;
+  rd.binv = fast_rcp(B);
 }
 
 // Solve in place: E holds d for the lane's rows on entry and x on exit.
@@ -112,7 +134,7 @@ __device__ __forceinline__ void tri_solve(const float* __restrict__ SUB, const f
   if (lane == kWarp - 1) e0n = 0.f;
   float D = dlast - rd.cl * e0n;
 #pragma unroll
-  for (int l = 0; l < 5; ++l) {
+  for (int l = 0; l < 5; ++l) {   // skipped levels carry zero multipliers
     const int s = 1 << l;
     float Dm = __shfl_up_sync(SFD_FULL, D, s);
     float Dp = __shfl_down_sync(SFD_FULL, D, s);
@@ -156,26 +178,38 @@ __device__ __forceinline__ float interp2(const float* __restrict__ A, int node, 
 // Bow friction: solve v + c phi(v) = b with phi(v) = sign(v)(eps + (1-eps)
 // e^{-a|v|}) (Sec. 3.3.1, Eq. 5).  Sticking (v = 0, phi = b/c) whenever
 // |b| <= c; otherwise the root of the convex g(w) = w + c phi(w) - |b| on
-// (0, |b|).  Newton from w = |b| (right of the root) decreases monotonically
-// for a convex increasing g, so it stops as soon as an iterate fails to
-// decrease (the root within FP32 rounding) or g, g' leave their signs.
-__device__ __forceinline__ float bow_phi(float b, float c, float a, float eps) {
+// (0, |b|).  Newton from a point right of the root decreases monotonically
+// for a convex g increasing there, so it stops as soon as an iterate fails
+// to decrease (the root within FP32 rounding).  The start is the previous
+// slip speed w_warm when it lies right of the root, its tangent root when it
+// lies left (right of the root by convexity), else |b|; w_warm is updated.
+__device__ __forceinline__ float bow_phi(float b, float c, float a, float eps, float& w_warm) {
   if (!(c > 0.f)) {
     const float w = fabsf(b);
     return b == 0.f ? 0.f : copysignf(eps + (1.f - eps) * expf(-a * w), b);
   }
   if (fabsf(b) <= c) return b / c;
   const float B = fabsf(b);
+  const float a2 = a * 1.44269504088896341f;   // e^{-a w} = 2^{-a2 w}
+  const float ce = c * (1.f - eps), c0 = c * eps - B;
   float w = B;
+  if (w_warm > 0.f && w_warm < B) {
+    const float ex = exp2f(-a2 * w_warm);
+    const float g = w_warm + c0 + ce * ex;
+    const float dg = 1.f - ce * a * ex;
+    if (g >= 0.f) w = w_warm;
+    else if (dg > 0.f) w = fminf(w_warm - __fdividef(g, dg), B);
+  }
   for (int it = 0; it < 32; ++it) {
-    const float ex = expf(-a * w);
-    const float g = w + c * (eps + (1.f - eps) * ex) - B;
-    const float dg = 1.f - c * (1.f - eps) * a * ex;
+    const float ex = exp2f(-a2 * w);
+    const float g = w + c0 + ce * ex;
+    const float dg = 1.f - ce * a * ex;
     if (!(g > 0.f) || !(dg > 0.f)) break;
-    const float wn = fmaxf(w - g / dg, 0.f);
+    const float wn = fmaxf(w - __fdividef(g, dg), 0.f);
     if (!(wn < w)) break;
     w = wn;
   }
+  w_warm = w;
   return copysignf(eps + (1.f - eps) * expf(-a * w), b);
 }
 

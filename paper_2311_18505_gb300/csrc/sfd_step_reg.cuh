@@ -82,10 +82,10 @@ __device__ __forceinline__ void tri_factor_r(const float (&sb)[MU], float (&iv)[
   for (int r = 0; r < MU; ++r) {
     float inv;
     if (r == 0) {
-      inv = __frcp_rn(iv[r]);
+      inv = fast_rcp(iv[r]);
       al[r] = sb[r] * inv;
     } else {
-      inv = __frcp_rn(iv[r] - sb[r] * cprev);
+      inv = fast_rcp(iv[r] - sb[r] * cprev);
       al[r] = -sb[r] * alprev * inv;
     }
     cp[r] = cp[r] * inv;
@@ -106,8 +106,12 @@ __device__ __forceinline__ void tri_factor_r(const float (&sb)[MU], float (&iv)[
   const float cl = cp[MU - 1];
   float A = al[MU - 1], B = 1.f + cl * g0n, C = cl * f0n;
   rd.cl = cl;
+  rd.nlev = 5;
+#pragma unroll
+  for (int l = 0; l < 5; ++l) { rd.k1[l] = 0.f; rd.k2[l] = 0.f; }
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
+    if (__all_sync(SFD_FULL, fabsf(A) + fabsf(C) <= kPcrDrop * fabsf(B))) { rd.nlev = l; break; }
     const int s = 1 << l;
     float Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
     float Cm = __shfl_up_sync(SFD_FULL, C, s);
@@ -115,14 +119,14 @@ __device__ __forceinline__ void tri_factor_r(const float (&sb)[MU], float (&iv)[
     float Cp = __shfl_down_sync(SFD_FULL, C, s);
     if (lane < s) { Am = 0.f; Bm = 1.f; Cm = 0.f; }
     if (lane + s >= kWarp) { Ap = 0.f; Bp = 1.f; Cp = 0.f; }
-    const float k1 = A * __frcp_rn(Bm), k2 = C * __frcp_rn(Bp);
+    const float k1 = A * fast_rcp(Bm), k2 = C * fast_rcp(Bp);
     A = -Am * k1;
     C = -Cp * k2;
     B = B - Cm * k1 - Ap * k2;
     rd.k1[l] = k1;
     rd.k2[l] = k2;
   }
-  rd.binv = __frcp_rn(B);
+  rd.binv = fast_rcp(B);
 }
 
 // Solve one (NR = 1) or two (NR = 2) right-hand sides in place, interleaved.
@@ -156,7 +160,7 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
   if (lane == kWarp - 1) { e1 = 0.f; e2 = 0.f; }
   float D1 = dl1 - rd.cl * e1, D2 = dl2 - rd.cl * e2;
 #pragma unroll
-  for (int l = 0; l < 5; ++l) {
+  for (int l = 0; l < 5; ++l) {   // skipped levels carry zero multipliers
     const int s = 1 << l;
     float m1 = __shfl_up_sync(SFD_FULL, D1, s), q1 = __shfl_down_sync(SFD_FULL, D1, s);
     float m2 = 0.f, q2 = 0.f;
@@ -177,6 +181,27 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
   for (int r = 0; r < MU; ++r) {
     x1[r] = x1[r] + ff[r] * X1 + gg[r] * Xp1;
     if (NR == 2) x2[r] = x2[r] + ff[r] * X2 + gg[r] * Xp2;
+  }
+}
+
+// Visit the lane's longitudinal rows i = lane + 32 k (k < m_z): full groups
+// of 4 rows compute all four results before any store (so the loads of the
+// group overlap), the remainder row by row.  fn(i, v, x) computes,
+// st(i, v, x) stores.
+template <class Fn, class St>
+__device__ __forceinline__ void z_rows(int m_z, int lane, Fn fn, St st) {
+  int k = 0;
+  for (; k + 4 <= m_z; k += 4) {
+    float v[4], x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fn(lane + kWarp * (k + q), v[q], x[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st(lane + kWarp * (k + q), v[q], x[q]);
+  }
+  for (; k < m_z; ++k) {
+    float v, x;
+    fn(lane + kWarp * k, v, x);
+    st(lane + kWarp * k, v, x);
   }
 }
 
@@ -211,13 +236,15 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   float *E2Z = nullptr, *E3Z = nullptr, *SUBZ = nullptr, *INVZ = nullptr, *CPZ = nullptr, *ALZ = nullptr;
   float *FFZ = nullptr, *GGZ = nullptr;
   int *ZLO = nullptr, *ZHI = nullptr;
-  float *ZW0 = nullptr, *ZW1 = nullptr, *ZMK = nullptr;
+  float* ZMK = nullptr;
+  float *SF0 = nullptr, *SF1 = nullptr, *SX0 = nullptr, *SX1 = nullptr;   // scatter slots
   if (has_z) {
     auto Z_ = [&]() { float* a = p + 2; p += RZ; return a; };
     Z = Z_(); DZ = Z_(); AZ = Z_(); XZ = Z_(); RZ_ = Z_(); E1Z = Z_(); E2Z = Z_(); E3Z = Z_();
     ZLO = reinterpret_cast<int*>(Z_());
     ZHI = reinterpret_cast<int*>(Z_());
-    ZW0 = Z_(); ZW1 = Z_(); ZMK = Z_();
+    ZMK = Z_();
+    SF0 = Z_(); SF1 = Z_(); SX0 = Z_(); SX1 = Z_();
     if (!zjac) {
       SUBZ = Z_(); INVZ = Z_(); CPZ = Z_(); ALZ = Z_(); FFZ = Z_(); GGZ = Z_();
     }
@@ -240,27 +267,27 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   }
   Scalars* scp = Dp->sc;
   int64_t n = scp->n, jnext = scp->next_out;
-  float uh = scp->uh, duh = scp->duh;
+  float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w, scz = scp->scale_z, scx = scp->scale_x;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
   int64_t sweeps_total = scp->sweeps_total;
 
   // grid transfer maps (exact integer positions)
   if (has_z) {
+    // pad rows (i >= n_u) point at longitudinal node N_l + 1 (a zero cell)
+    // with weight 0, so every lane can interpolate and scatter
+    // unconditionally (no divergent branches)
 #pragma unroll
     for (int r = 0; r < MU; ++r) {
       const int i = ub + r;
-      if (i < n_u) {
-        const int pos = (i + 1) * n_l;
-        const int mm = pos / n_t;
-        TMIs[i] = mm;
-        TMWs[i] = static_cast<float>(pos - mm * n_t) / static_cast<float>(n_t);
-      }
+      const int pos = (i + 1) * n_l;
+      const int mm = i < n_u ? pos / n_t : n_l + 1;
+      TMIs[i] = mm;
+      TMWs[i] = i < n_u ? static_cast<float>(pos - mm * n_t) / static_cast<float>(n_t) : 0.f;
     }
-    // longitudinal row i (node mm = i + 1) gathers from transverse nodes
-    // [lo, hi]; when N_l >= N_t that range holds at most two nodes, whose
-    // hat weights are stored (w0 for lo, w1 for lo + 1).  Pad rows get an
-    // empty range, zero weights and a zero mask.
+    // longitudinal row i (node mm = i + 1) gathers from the transverse nodes
+    // [lo, hi] of its hat support (at most four nodes when N_t <= 2 N_l).
+    // Pad rows get an empty range and a zero mask.
     for (int i = lane; i < kWarp * m_z; i += kWarp) {
       const int mm = i + 1;
       int lo = ((mm - 1) * n_t) / n_l + 1;
@@ -270,13 +297,10 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       if (i >= n_z) { lo = 1; hi = 0; }
       ZLO[i] = lo;
       ZHI[i] = hi;
-      const int d0 = lo * n_l - mm * n_t, d1 = (lo + 1) * n_l - mm * n_t;
-      ZW0[i] = lo <= hi ? 1.f - static_cast<float>(d0 < 0 ? -d0 : d0) / static_cast<float>(n_t) : 0.f;
-      ZW1[i] = lo + 1 <= hi ? 1.f - static_cast<float>(d1 < 0 ? -d1 : d1) / static_cast<float>(n_t) : 0.f;
       ZMK[i] = i < n_z ? 1.f : 0.f;
     }
   }
-  const bool two_slot = n_l >= n_t;
+  const bool four_slot = n_t <= 2 * n_l;
   __syncwarp();
   const float inv_nt = 1.f / static_cast<float>(n_t);
   auto interp_z = [&](const float* A, int i) {
@@ -284,23 +308,69 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     const float w = TMWs[i];
     return (1.f - w) * A[mm - 1] + w * A[mm];
   };
-  auto spread = [&](const float* F, int i) {
+  // (P^T F) at longitudinal row i: hat weights 1 - |l N_l - mm N_t| / N_t
+  // computed from integers, zero outside the support.
+  auto spread4 = [&](const float* F, int i) {
     const int lo = ZLO[i];
-    if (two_slot) return ZW0[i] * F[lo - 1] + ZW1[i] * F[lo];
-    const int mm = i + 1, hi = ZHI[i];
+    const int d0 = lo * n_l - (i + 1) * n_t;
     float acc = 0.f;
-    for (int l = lo; l <= hi; ++l) {
-      const int dd = l * n_l - mm * n_t;
-      const float w = 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dd = d0 + q * n_l;
+      const float w = fmaxf(0.f, 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt);
+      acc = fmaf(w, F[lo - 1 + q], acc);
+    }
+    return acc;
+  };
+  // wide supports (N_t > 2 N_l): a warp-uniform trip count kz covers every
+  // row's support; weights beyond a row's own support are zero and their
+  // indices stay inside the transverse transfer array (pad rows hold zeros)
+  const int kz = (2 * n_t + n_l - 1) / n_l + 1;
+  auto spreadL = [&](const float* F, int i) {
+    const int lo = ZLO[i];
+    const int d0 = lo * n_l - (i + 1) * n_t;
+    float acc = 0.f;
+    for (int q = 0; q < kz; ++q) {
+      const int dd = d0 + q * n_l;
+      const float w = fmaxf(0.f, 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt);
+      const int l = lo + q < n_t ? lo + q : n_t - 1;
       acc = fmaf(w, F[l - 1], acc);
     }
     return acc;
+  };
+  // transfer form: 2 = scatter from the transverse nodes (N_l >= N_t: each
+  // transverse node sits in its own longitudinal interval, so node l alone
+  // writes slot S0[m_l] and slot S1[m_l + 1]; the written set is fixed and
+  // every other slot stays zero); 4 = four-slot gather; 0 = wide gather
+  const int zform = n_l >= n_t ? 2 : (four_slot ? 4 : 0);
+  auto emit = [&](const float (&f)[MU], float* G, float* S0, float* S1) {
+    if (zform == 2) {
+#pragma unroll
+      for (int r = 0; r < MU; ++r) {
+        const int mm = TMIs[ub + r];
+        const float w = TMWs[ub + r];
+        S0[mm] = (1.f - w) * f[r];
+        S1[mm + 1] = w * f[r];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < MU; ++r) G[ub + r] = f[r];
+    }
+  };
+  auto spreadS = [&](const float* S0, const float* S1, int i) { return S0[i + 1] + S1[i + 1]; };
+  auto spread = [&](const float* F, int i) {
+    if (zform == 2) return F == FV ? spreadS(SF0, SF1, i) : spreadS(SX0, SX1, i);
+    return zform == 4 ? spread4(F, i) : spreadL(F, i);
   };
 
   // ---- constant matrices ----
   Red rdu, rdz;
   const float dz_diag = 1.f + s0 + 2.f * s1l;
-  const float dz_inv = __frcp_rn(dz_diag);
+  const float dz_inv = fast_rcp(dz_diag);
+  auto z_axpy = [&](float a) {        // AZ += a XZ over the lane's longitudinal rows
+    z_rows(m_z, lane, [&](int i, float& v, float&) { v = fmaf(a, XZ[i], AZ[i]); },
+           [&](int i, float v, float) { AZ[i] = v; });
+  };
   if (has_z && !zjac) {
     for (int r = 0; r < m_z; ++r) {
       const int i = lane * m_z + r;
@@ -386,21 +456,23 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       extend<MU>(U, Ue, lane);
       extend1<MU>(DU, DUe, lane);
 #pragma unroll
-      for (int r = 0; r < MU; ++r) {
-        GL[r] = Ue[r + 2] - Ue[r + 1];
-        GR[r] = Ue[r + 3] - Ue[r + 2];
+      for (int r = 0; r < MU; ++r) {   // interval differences; zero on pad rows
+        const bool real = ub + r < n_u;
+        GL[r] = real ? Ue[r + 2] - Ue[r + 1] : 0.f;
+        GR[r] = real ? Ue[r + 3] - Ue[r + 2] : 0.f;
       }
       float ZTe[MU + 2];
       if (has_z) {
         float zt[MU];
 #pragma unroll
-        for (int r = 0; r < MU; ++r) zt[r] = (ub + r < n_u) ? interp_z(Z, ub + r) : 0.f;
+        for (int r = 0; r < MU; ++r) zt[r] = interp_z(Z, ub + r);
         extend1<MU>(zt, ZTe, lane);
       }
-      float RA[MU];
+      float RA[MU], fv[MU];
 #pragma unroll
       for (int r = 0; r < MU; ++r) {
         const int i = ub + r;
+        fv[r] = 0.f;
         const float u0 = Ue[r + 2], um1 = Ue[r + 1], up1 = Ue[r + 3], um2 = Ue[r], up2 = Ue[r + 4];
         const float gl = GL[r], gr = GR[r];
         const float d2 = gr - gl;
@@ -416,17 +488,17 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
           if (has_z) {
             yl += 4.f * cb * gl * (ZTe[r + 1] - ZTe[r]);
             yr += 4.f * cb * gr * (ZTe[r + 2] - ZTe[r + 1]);
-            if (i < n_u) FV[i] = gr2 - gl2;
+            fv[r] = gr2 - gl2;   // zero on pad rows
           }
           rhs += yr - yl;
-          if (i < n_u) {
-            SB[r] = i > 0 ? tho - s1 - ca * gl2 : 0.f;
-            IV[r] = th + s0 + 2.f * s1 + ca * (gl2 + gr2);
-            CPr[r] = i < n_u - 1 ? tho - s1 - ca * gr2 : 0.f;
-          }
+          const bool real = i < n_u;
+          SB[r] = (real && i > 0) ? tho - s1 - ca * gl2 : 0.f;
+          IV[r] = real ? th + s0 + 2.f * s1 + ca * (gl2 + gr2) : 1.f;
+          CPr[r] = i < n_u - 1 ? tho - s1 - ca * gr2 : 0.f;
         }
         RA[r] = i < n_u ? rhs : 0.f;
       }
+      if (has_z) emit(fv, FV, SF0, SF1);
       if (!linear) tri_factor_r<MU>(SB, IV, CPr, FFr, GGr, lane, rdu);
       __syncwarp();
 
@@ -441,78 +513,96 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         }
       } else {
         // ---- stage 2: longitudinal right-hand side ----
-#pragma unroll 2
-        for (int k = 0; k < m_z; ++k) {
-          const int i = lane + kWarp * k;
-          const float z0 = Z[i];
-          const float d2z = (Z[i + 1] - z0) - (z0 - Z[i - 1]);
-          const float dz0 = DZ[i];
-          const float d2dz = (DZ[i + 1] - dz0) - (dz0 - DZ[i - 1]);
-          RZ_[i] = ZMK[i] * (lam2l * d2z - 2.f * s0 * dz0 + 2.f * s1l * d2dz + 2.f * cz * spread(FV, i));
+        float dzmax = 0.f;   // lane's largest |Dz|: scale of the longitudinal increments
+        {
+          auto rhs_row = [&](int i, auto sp) {
+            const float z0 = Z[i], dz0 = DZ[i];
+            const float d2z = (Z[i + 1] - z0) - (z0 - Z[i - 1]);
+            const float d2dz = (DZ[i + 1] - dz0) - (dz0 - DZ[i - 1]);
+            dzmax = fmaxf(dzmax, fabsf(dz0));
+            const float v = lam2l * d2z - 2.f * s0 * dz0 + 2.f * s1l * d2dz + 2.f * cz * sp(FV, i);
+            return i < n_z ? v : 0.f;
+          };
+          auto st = [&](int i, float v, float) { RZ_[i] = v; };
+          auto sps = [&](const float*, int i) { return spreadS(SF0, SF1, i); };
+          if (zform == 2)
+            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, sps); }, st);
+          else if (zform == 4)
+            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, spread4); }, st);
+          else
+            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, spreadL); }, st);
         }
         __syncwarp();
         // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
         int sweep = 0;
-        float e_prev = 0.f;
+        float e_prev = 0.f, mag_all = 0.f, mgx_all = 0.f;
         for (;;) {
           float az[MU], AZe[MU + 2];
 #pragma unroll
-          for (int r = 0; r < MU; ++r) az[r] = (ub + r < n_u) ? interp_z(AZ, ub + r) : 0.f;
+          for (int r = 0; r < MU; ++r) az[r] = interp_z(AZ, ub + r);
           extend1<MU>(az, AZe, lane);
 #pragma unroll
           for (int r = 0; r < MU; ++r)
-            AC[r] = (ub + r < n_u) ? RA[r] + cb * (GR[r] * (AZe[r + 2] - AZe[r + 1]) - GL[r] * (AZe[r + 1] - AZe[r]))
-                                   : 0.f;
+            AC[r] = RA[r] + cb * (GR[r] * (AZe[r + 2] - AZe[r + 1]) - GL[r] * (AZe[r + 1] - AZe[r]));
           if (need_resp) {
             float xz[MU], XZe[MU + 2];
 #pragma unroll
-            for (int r = 0; r < MU; ++r) xz[r] = (ub + r < n_u) ? interp_z(XZ, ub + r) : 0.f;
+            for (int r = 0; r < MU; ++r) xz[r] = interp_z(XZ, ub + r);
             extend1<MU>(xz, XZe, lane);
             load_J(XP);
 #pragma unroll
             for (int r = 0; r < MU; ++r)
-              if (ub + r < n_u)
-                XP[r] += cb * (GR[r] * (XZe[r + 2] - XZe[r + 1]) - GL[r] * (XZe[r + 1] - XZe[r]));
+              XP[r] += cb * (GR[r] * (XZe[r + 2] - XZe[r + 1]) - GL[r] * (XZe[r + 1] - XZe[r]));
             tri_solve_r<MU, 2>(SB, IV, CPr, FFr, GGr, AC, XP, lane, rdu);
           } else {
             tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
           }
           // nodal d_+[g d(.)] of the new accelerations for the longitudinal rows
           {
-            float ACe[MU + 2];
+            float ACe[MU + 2], fc[MU];
             extend1<MU>(AC, ACe, lane);
 #pragma unroll
             for (int r = 0; r < MU; ++r)
-              if (ub + r < n_u)
-                FV[ub + r] = GR[r] * (ACe[r + 2] - ACe[r + 1]) - GL[r] * (ACe[r + 1] - ACe[r]);
+              fc[r] = GR[r] * (ACe[r + 2] - ACe[r + 1]) - GL[r] * (ACe[r + 1] - ACe[r]);
+            emit(fc, FV, SF0, SF1);
             if (need_resp) {
               float XPe[MU + 2];
               extend1<MU>(XP, XPe, lane);
 #pragma unroll
               for (int r = 0; r < MU; ++r)
-                if (ub + r < n_u)
-                  XFC[ub + r] = GR[r] * (XPe[r + 2] - XPe[r + 1]) - GL[r] * (XPe[r + 1] - XPe[r]);
+                fc[r] = GR[r] * (XPe[r + 2] - XPe[r + 1]) - GL[r] * (XPe[r + 1] - XPe[r]);
+              emit(fc, XFC, SX0, SX1);
             }
           }
           __syncwarp();
           float chg = 0.f, mag = 0.f, chx = 0.f, mgx = 0.f;
           if (zjac) {
             // one Jacobi update of each field into the spare buffer, then swap
-#pragma unroll 2
-            for (int k = 0; k < m_z; ++k) {
-              const int i = lane + kWarp * k;
-              const float mk = ZMK[i];
-              const float v = mk * (RZ_[i] + cz * spread(FV, i) + s1l * (AZ[i - 1] + AZ[i + 1])) * dz_inv;
+            auto jac = [&](int i, float& v, float& x, auto sp, auto spx) {
+              const bool real = i < n_z;
+              v = (RZ_[i] + cz * sp(FV, i) + s1l * (AZ[i - 1] + AZ[i + 1])) * dz_inv;
+              v = real ? v : 0.f;
               chg = fmaxf(chg, fabsf(v - AZ[i]));
-              mag = fmaxf(mag, fmaxf(fabsf(v), fabsf(DZ[i])));
-              E2Z[i] = v;
+              mag = fmaxf(mag, fabsf(v));
               if (need_resp) {
-                const float x = mk * (cz * spread(XFC, i) + s1l * (XZ[i - 1] + XZ[i + 1])) * dz_inv;
+                x = (cz * spx(XFC, i) + s1l * (XZ[i - 1] + XZ[i + 1])) * dz_inv;
+                x = real ? x : 0.f;
                 chx = fmaxf(chx, fabsf(x - XZ[i]));
                 mgx = fmaxf(mgx, fabsf(x));
-                E3Z[i] = x;
               }
-            }
+            };
+            auto st = [&](int i, float v, float x) {
+              E2Z[i] = v;
+              if (need_resp) E3Z[i] = x;
+            };
+            auto sps = [&](const float*, int i) { return spreadS(SF0, SF1, i); };
+            auto spx = [&](const float*, int i) { return spreadS(SX0, SX1, i); };
+            if (zform == 2)
+              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, sps, spx); }, st);
+            else if (zform == 4)
+              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, spread4, spread4); }, st);
+            else
+              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, spreadL, spreadL); }, st);
             __syncwarp();
             { float* t = AZ; AZ = E2Z; E2Z = t; }
             if (need_resp) { float* t = XZ; XZ = E3Z; E3Z = t; }
@@ -544,19 +634,25 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
               }
             }
           }
-          chg = warp_max_nonneg(chg);
-          mag = warp_max_nonneg(mag);
-          chx = warp_max_nonneg(chx);
-          mgx = warp_max_nonneg(mgx);
-          __syncwarp();
+          // relative change: each field against the larger of its magnitude
+          // in this lane and its string-wide scale from the previous step,
+          // so one warp reduction per sweep suffices
+          mag = fmaxf(mag, dzmax);
+          float el = chg > 0.f ? chg / fmaxf(mag, scz) : 0.f;
+          if (need_resp) el = fmaxf(el, chx > 0.f ? chx / fmaxf(mgx, scx) : 0.f);
+          mag_all = fmaxf(mag_all, mag);
+          mgx_all = fmaxf(mgx_all, mgx);
+          const float e = warp_max_nonneg(el);
           ++sweep;
-          const float e = fmaxf(chg > 0.f ? chg / mag : 0.f, chx > 0.f ? chx / mgx : 0.f);
           if (sweep_converged(e, e_prev, sweep)) break;
           if (sweep >= kMaxSweeps) { status |= kStNoConv; break; }
           e_prev = e;
         }
         sweeps_total += sweep;
         if (sweep > max_sweeps) max_sweeps = sweep;
+        // string-wide scales for the next step's convergence test
+        scz = warp_max_nonneg(mag_all);
+        if (need_resp) scx = warp_max_nonneg(mgx_all);
       }
 
       // ---- stage 4: excitation force (scalar elimination) ----
@@ -572,44 +668,30 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         if (s != 0.f) {
 #pragma unroll
           for (int r = 0; r < MU; ++r) AC[r] = fmaf(s, XP[r], AC[r]);
-          if (has_z)
-            for (int k = 0; k < m_z; ++k) {
-              const int i = lane + kWarp * k;
-              AZ[i] = fmaf(s, XZ[i], AZ[i]);
-            }
+          if (has_z) z_axpy(s);
         }
       } else if (exc == kBow && FB > 0.f) {
         const float b = (node_interp<MU>(AC, en, ew, n_u) + 2.f * node_interp<MU>(DU, en, ew, n_u)) / (2.f * kk) -
                         bow_v;
         const float c = 0.5f * kk * FB * node_interp<MU>(XP, en, ew, n_u);
-        const float phi = bow_phi(b, c, bow_a, bow_eps);
+        const float phi = bow_phi(b, c, bow_a, bow_eps, bow_w);
         const float s = -k2 * FB * phi;
 #pragma unroll
         for (int r = 0; r < MU; ++r) AC[r] = fmaf(s, XP[r], AC[r]);
-        if (has_z)
-          for (int k = 0; k < m_z; ++k) {
-            const int i = lane + kWarp * k;
-            AZ[i] = fmaf(s, XZ[i], AZ[i]);
-          }
+        if (has_z) z_axpy(s);
       }
 
       // ---- stage 5: advance the time level ----
       bool bad = false;
 #pragma unroll
-      for (int r = 0; r < MU; ++r) {
-        if (ub + r < n_u) {
-          DU[r] = DU[r] + AC[r];
-          U[r] = U[r] + DU[r];
-          bad |= !isfinite(U[r]);
-        }
+      for (int r = 0; r < MU; ++r) {   // pad rows stay zero (their accelerations are zero)
+        DU[r] = DU[r] + AC[r];
+        U[r] = U[r] + DU[r];
+        bad |= !isfinite(U[r]);
       }
       if (has_z) {
-        for (int k = 0; k < m_z; ++k) {
-          const int i = lane + kWarp * k;
-          const float d = DZ[i] + AZ[i];
-          DZ[i] = d;
-          Z[i] += d;
-        }
+        z_rows(m_z, lane, [&](int i, float& d, float& z) { d = DZ[i] + AZ[i]; z = Z[i] + d; },
+               [&](int i, float d, float z) { DZ[i] = d; Z[i] = z; });
       }
       if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
       __syncwarp();
@@ -647,6 +729,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     scp->next_out = jnext;
     scp->uh = uh;
     scp->duh = duh;
+    scp->bow_w = bow_w;
+    scp->scale_z = scz;
+    scp->scale_x = scx;
     scp->status = status;
     scp->max_sweeps = max_sweeps;
     scp->sweeps_total = sweeps_total;

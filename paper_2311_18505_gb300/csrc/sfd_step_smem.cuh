@@ -65,7 +65,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   }
   Scalars* scp = Dp->sc;
   int64_t n = scp->n, jnext = scp->next_out;
-  float uh = scp->uh, duh = scp->duh;
+  float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
   int64_t sweeps_total = scp->sweeps_total;
@@ -376,7 +376,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         const float k = Dp->k;
         const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) / (2.f * k) - Dp->bow_v;
         const float c = 0.5f * k * FB * interp2(XP, en, ew);
-        const float phi = bow_phi(b, c, Dp->bow_a, Dp->bow_eps);
+        const float phi = bow_phi(b, c, Dp->bow_a, Dp->bow_eps, bow_w);
         const float s = -Dp->k2 * FB * phi;
         for (int r = 0; r < m_u; ++r) AC[ub + r] = fmaf(s, XP[ub + r], AC[ub + r]);
         if (has_z)
@@ -438,6 +438,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
     scp->next_out = jnext;
     scp->uh = uh;
     scp->duh = duh;
+    scp->bow_w = bow_w;
     scp->status = status;
     scp->max_sweeps = max_sweeps;
     scp->sweeps_total = sweeps_total;

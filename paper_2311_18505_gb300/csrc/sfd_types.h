@@ -22,6 +22,10 @@ struct Scalars {
   int32_t status;         // StatusBits
   int32_t max_sweeps;     // largest sweep count seen (diagnostic)
   int64_t sweeps_total;   // total coupled-solve sweeps (diagnostic)
+  float bow_w;            // last bow slip speed |v_rel| (Newton warm start)
+  float scale_z;          // string-wide scale of the longitudinal increment (solver test)
+  float scale_x;          // string-wide scale of the unit-force response (solver test)
+  float pad_;
 };
 
 // Per-string descriptor (device memory, read-only in the kernel).
@@ -88,7 +92,7 @@ constexpr int kArraysU = 19;
 constexpr int kArraysZ = 15;
 inline __host__ __device__ int warp_smem_floats(int m_u, int m_z, int z_jacobi) {
   const int ru = kWarp * m_u + 4, rz = m_z > 0 ? kWarp * m_z + 4 : 0;
-  if (m_u <= kMaxRegRows && (m_u & 1)) return 4 * ru + (z_jacobi ? 13 : 19) * rz;
+  if (m_u <= kMaxRegRows && (m_u & 1)) return 4 * ru + (z_jacobi ? 15 : 21) * rz;
   return kArraysU * ru + kArraysZ * rz;
 }
 
