@@ -182,6 +182,42 @@ sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint6
 
 sfd_status sfd_batch_destroy(sfd_batch* b);
 
+/* Excitation of a string for sfd_synthesize_noalloc (same meaning and units
+ * as the sfd_excite_* calls).  kind: 0 pluck (amp_m, pos), 1 hammer
+ * (mass_kg, vel_mps, pos, omega_h, alpha_h), 2 bow (vel_mps, force_n, pos,
+ * a_s_per_m, eps, release_time_s). */
+typedef struct {
+  int32_t kind;
+  int32_t pad_;
+  double amp_m, pos;
+  double mass_kg, vel_mps, omega_h, alpha_h;
+  double force_n, a_s_per_m, eps, release_time_s;
+} sfd_excitation;
+
+/* Largest scratch a string may need in sfd_synthesize_noalloc (descriptor,
+ * state, job entry and counters, 256-byte aligned). */
+#define SFD_NOALLOC_SCRATCH_BYTES (32u * 1024u)
+
+/* Synthesize the first n_samples output samples of one string, set up from
+ * `params` and `exc` exactly as sfd_string_create + sfd_excite_* would, into
+ * out_device (device memory on `device`), without allocating any device
+ * memory.  For callers that cannot call cudaMalloc: real-time audio threads
+ * (it can synchronise the device and block for an unbounded time), code
+ * running while a stream is captured, hosts that fix a library's device
+ * footprint in advance.  There is no counterpart in the paper.
+ *
+ * The string's descriptor, state, job entry and work-queue counter live in
+ * one static device array of SFD_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library keeps until the process exits; strings that need
+ * more get SFD_EINVAL.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current: make it
+ * before any stream capture.  Every call shares the array and overwrites it,
+ * so calls that overlap on the GPU (from several threads or streams) race:
+ * serialise them.  The call waits for its stream before returning (it reads
+ * the string's status).  f0 modulation is not available here. */
+sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, const sfd_string_params* params,
+                                  const sfd_excitation* exc, int64_t n_samples, float* out_device);
+
 /* Thread-local message describing the last error. */
 const char* sfd_last_error(void);
 

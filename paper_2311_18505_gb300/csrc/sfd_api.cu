@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -873,3 +874,193 @@ sfd_status sfd_batch_destroy(sfd_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Synthesis without device allocation.
+//
+// Callers that must not allocate device memory -- a real-time audio callback
+// (cudaMalloc can synchronise the device and block for an unbounded time),
+// code running while a stream is being captured into a CUDA graph, or a host
+// that fixes a library's device footprint up front -- use this one entry
+// point instead of a context.  Everything the step kernel needs beyond the
+// caller's output buffer (the string's descriptor and state, the job entry
+// and the work-queue counter) lives in one file-scope device array of
+// kNoAllocBytes, which every GPU that loads this library keeps until exit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 32u * 1024u;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};      // device address of the array, per device
+size_t g_noalloc_smem[kMaxDevices] = {};    // opt-in shared memory per block, per device
+
+}  // namespace
+
+extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, const sfd_string_params* params,
+                                             const sfd_excitation* exc, int64_t n_samples, float* out_device) {
+  if (!params || !exc) return fail(SFD_EINVAL, "params and excitation are required");
+  if (n_samples < 0) return fail(SFD_EINVAL, "n_samples < 0");
+  if (n_samples > 0 && !out_device) return fail(SFD_EINVAL, "out_device is NULL");
+  if (device < 0 || device >= kMaxDevices) return fail(SFD_EINVAL, "device %d out of range", device);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  void* base = nullptr;
+  size_t smem_optin = 0;
+  {
+    // once per device, with that device current: the array's device address
+    // (a host-side reference to it is only a stand-in, not usable by kernels)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+      int optin = 0;
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+      g_noalloc_ptr[device] = p;
+      g_noalloc_smem[device] = static_cast<size_t>(optin);
+    }
+    base = g_noalloc_ptr[device];
+    smem_optin = g_noalloc_smem[device];
+  }
+  if (n_samples == 0) return SFD_OK;
+
+  // the string, as sfd_string_create + sfd_excite_* would set it up
+  sfd_string s;
+  s.p = *params;
+  sfd_string_params& q = s.p;
+  if (q.length_m == 0) q.length_m = 1.0;
+  if (q.fs == 0) q.fs = 48000.0;
+  if (q.linear_density == 0) q.linear_density = 5e-3;
+  if (q.theta == 0) q.theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
+  if (q.pickup_pos == 0) q.pickup_pos = 0.7;
+  if (q.f0_max_ratio < 1.0) q.f0_max_ratio = 1.0;
+  const double gamma = q.gamma > 0 ? q.gamma : 2.0 * q.f0;
+  if (!(gamma > 0) || !std::isfinite(gamma) || !(q.fs > 0) || !(q.kappa >= 0) || !(q.alpha >= 1.0) ||
+      !(q.sigma0 >= 0) || !(q.sigma1 >= 0) || !(q.theta > 0.5 && q.theta <= 1.0) ||
+      !(q.pickup_pos > 0 && q.pickup_pos < 1) || !(q.length_m > 0) || !(q.linear_density > 0) ||
+      (q.boundary != 0 && q.boundary != 1) || (q.grid_rule != 0 && q.grid_rule != 1))
+    return fail(SFD_EINVAL, "invalid string parameters");
+  int n_t = 0, n_l = 0;
+  sfd_status rc = derive_grid(q, gamma * q.f0_max_ratio, &n_t, &n_l);
+  if (rc) return rc;
+  s.gamma = gamma;
+  s.k = 1.0 / q.fs;
+  s.n_t = n_t;
+  s.n_l = n_l;
+  s.h.bow_release_n = INT64_MAX;
+  const double pos = exc->pos;
+  if (!(pos > 0 && pos < 1)) return fail(SFD_EINVAL, "excitation position must be in (0, 1)");
+  if (exc->kind == kPluck) {
+    if (!std::isfinite(exc->amp_m)) return fail(SFD_EINVAL, "bad pluck amplitude");
+    s.exc = kPluck;
+    s.pluck_amp = exc->amp_m;
+    s.pluck_pos = pos;
+    fill_desc(&s);
+  } else if (exc->kind == kHammer) {
+    if (!(exc->mass_kg > 0) || !(exc->omega_h > 0) || !(exc->alpha_h >= 1) || !std::isfinite(exc->vel_mps))
+      return fail(SFD_EINVAL, "bad hammer parameters");
+    s.exc = kHammer;
+    fill_desc(&s);
+    point_weights(n_t, pos, &s.h.e_node, &s.h.e_w);
+    s.h.ham_M = static_cast<float>(exc->mass_kg / (q.linear_density * q.length_m));
+    s.h.ham_k2w = static_cast<float>(s.k * s.k * std::pow(exc->omega_h, 1.0 + exc->alpha_h));
+    s.h.ham_expo = static_cast<float>(exc->alpha_h - 1.0);
+    s.hammer_uh1 = (exc->vel_mps / q.length_m) * s.k;
+  } else if (exc->kind == kBow) {
+    if (!(exc->force_n >= 0) || !(exc->eps >= 0 && exc->eps <= 1) || !(exc->a_s_per_m >= 0) ||
+        !std::isfinite(exc->vel_mps))
+      return fail(SFD_EINVAL, "bad bow parameters");
+    s.exc = kBow;
+    fill_desc(&s);
+    point_weights(n_t, pos, &s.h.e_node, &s.h.e_w);
+    s.h.bow_F = static_cast<float>(exc->force_n / (q.linear_density * q.length_m * q.length_m));
+    s.h.bow_v = static_cast<float>(exc->vel_mps / q.length_m);
+    s.h.bow_a = static_cast<float>(exc->a_s_per_m * q.length_m);
+    s.h.bow_eps = static_cast<float>(exc->eps);
+    if (exc->release_time_s >= 0) {
+      int64_t n = static_cast<int64_t>(std::ceil(exc->release_time_s * q.fs));
+      while (n > 0 && static_cast<double>(n - 1) * s.k >= exc->release_time_s) --n;
+      while (static_cast<double>(n) * s.k < exc->release_time_s) ++n;
+      s.h.bow_release_n = n;
+    }
+  } else {
+    return fail(SFD_EINVAL, "bad excitation kind %d", exc->kind);
+  }
+  const Desc& D = s.h;
+  const size_t wbytes = static_cast<size_t>(warp_smem_floats(D.m_u, D.m_z, D.z_jacobi)) * sizeof(float);
+  if (wbytes > smem_optin) return fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", n_t, n_l);
+
+  // layout inside the array: Desc | Scalars | u du z dz xz az | Job | counters
+  const size_t nz = D.n_z > 0 ? D.n_z : 1;
+  size_t off = 0;
+  auto place = [&](size_t n) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    const size_t at = off;
+    off += n;
+    return at;
+  };
+  const size_t o_desc = place(sizeof(Desc)), o_sc = place(sizeof(Scalars));
+  const size_t o_u = place(sizeof(float) * D.n_u), o_du = place(sizeof(float) * D.n_u);
+  const size_t o_z = place(sizeof(float) * nz), o_dz = place(sizeof(float) * nz);
+  const size_t o_xz = place(sizeof(float) * nz), o_az = place(sizeof(float) * nz);
+  const size_t o_job = place(sizeof(Job)), o_cnt = place(sizeof(int) * kClasses);
+  if (off > kNoAllocBytes)
+    return fail(SFD_EINVAL,
+                "string needs %zu bytes of scratch (N_t=%d, N_l=%d); the no-allocation entry point holds %zu",
+                off, n_t, n_l, kNoAllocBytes);
+  char* b = static_cast<char*>(base);
+  s.h.u = reinterpret_cast<float*>(b + o_u);
+  s.h.du = reinterpret_cast<float*>(b + o_du);
+  s.h.z = reinterpret_cast<float*>(b + o_z);
+  s.h.dz = reinterpret_cast<float*>(b + o_dz);
+  s.h.xz = reinterpret_cast<float*>(b + o_xz);
+  s.h.az = reinterpret_cast<float*>(b + o_az);
+  s.h.sc = reinterpret_cast<Scalars*>(b + o_sc);
+
+  // initial levels w^0, w^1 (the array keeps the previous call's contents,
+  // so every field the kernel reads is written here)
+  std::vector<float> u(D.n_u, 0.f), zero(std::max<size_t>(nz, static_cast<size_t>(D.n_u)), 0.f);
+  Scalars sc{};
+  sc.n = 1;
+  sc.next_out = 0;
+  if (s.exc == kPluck && s.pluck_amp != 0.0) {
+    const double c0 = s.pluck_amp / q.length_m, xp = s.pluck_pos;
+    for (int l = 1; l < n_t; ++l) {
+      const double x = static_cast<double>(l) / n_t;
+      u[l - 1] = static_cast<float>(x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp));
+    }
+  }
+  if (s.exc == kHammer) {
+    sc.uh = static_cast<float>(s.hammer_uh1);
+    sc.duh = static_cast<float>(s.hammer_uh1);
+  }
+  const Job job{reinterpret_cast<const Desc*>(b + o_desc), out_device, n_samples};
+  struct Copy { size_t at; const void* src; size_t n; };
+  const Copy copies[] = {{o_desc, &s.h, sizeof(Desc)}, {o_sc, &sc, sizeof(Scalars)},
+                         {o_u, u.data(), sizeof(float) * D.n_u}, {o_du, zero.data(), sizeof(float) * D.n_u},
+                         {o_z, zero.data(), sizeof(float) * nz}, {o_dz, zero.data(), sizeof(float) * nz},
+                         {o_xz, zero.data(), sizeof(float) * nz}, {o_az, zero.data(), sizeof(float) * nz},
+                         {o_job, &job, sizeof(Job)}};
+  for (const Copy& cp : copies) {
+    e = cudaMemcpyAsync(b + cp.at, cp.src, cp.n, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy into the no-allocation scratch");
+  }
+  const int k = job_class(D);
+  int* counter = reinterpret_cast<int*>(b + o_cnt) + k;   // the launcher clears it on `stream`
+  e = kLaunch[k](reinterpret_cast<const Job*>(b + o_job), 1, counter,
+                 warp_smem_floats(D.m_u, D.m_z, D.z_jacobi), 1, 1, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  e = cudaMemcpyAsync(&sc, b + o_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  rc = status_code(sc);
+  if (rc == SFD_EUNSTABLE) return fail(rc, "string state became non-finite");
+  if (rc == SFD_ENOCONV) return fail(rc, "coupled solve reached its sweep cap (result kept)");
+  return SFD_OK;
+}

@@ -42,6 +42,18 @@ class sfd_string_params(ctypes.Structure):
     ]
 
 
+class sfd_excitation(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("amp_m", ctypes.c_double), ("pos", ctypes.c_double),
+        ("mass_kg", ctypes.c_double), ("vel_mps", ctypes.c_double), ("omega_h", ctypes.c_double),
+        ("alpha_h", ctypes.c_double), ("force_n", ctypes.c_double), ("a_s_per_m", ctypes.c_double),
+        ("eps", ctypes.c_double), ("release_time_s", ctypes.c_double),
+    ]
+
+
+SFD_NOALLOC_SCRATCH_BYTES = 32 * 1024
+
 _lib = None
 
 
@@ -77,6 +89,7 @@ def lib() -> ctypes.CDLL:
         "sfd_batch_destroy": (i32, [vp]),
         "sfd_last_launch_count": (i32, [vp]),
         "sfd_ctx_transfer_bytes": (i32, [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "sfd_synthesize_noalloc": (i32, [ctypes.c_int, vp, P(sfd_string_params), P(sfd_excitation), i64, vp]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -249,6 +262,28 @@ def sfd_ctx_transfer_bytes(ctx: int) -> tuple[int, int]:
 
 def sfd_last_error() -> str:
     return lib().sfd_last_error().decode(errors="replace")
+
+
+def excitation_from_dict(ex: dict) -> sfd_excitation:
+    e = sfd_excitation()
+    e.pos = ex["pos"]
+    if ex["kind"] == "pluck":
+        e.kind, e.amp_m = 0, ex["amp"]
+    elif ex["kind"] == "hammer":
+        e.kind, e.mass_kg, e.vel_mps = 1, ex["mass"], ex["vel"]
+        e.omega_h, e.alpha_h = ex.get("omega", 3000.0), ex.get("alpha", 2.5)
+    else:
+        e.kind, e.vel_mps, e.force_n = 2, ex["vel"], ex["force"]
+        e.a_s_per_m, e.eps, e.release_time_s = ex.get("a", 100.0), ex.get("eps", 0.1), ex.get("release", -1.0)
+    return e
+
+
+def sfd_synthesize_noalloc(device: int, stream, params: sfd_string_params, exc: sfd_excitation,
+                           n_samples: int, out_device) -> None:
+    """First n_samples samples of one string into device memory, with no
+    device allocation (scratch in the library's static device array)."""
+    ptr = out_device if isinstance(out_device, int) else out_device.data_ptr()
+    _check(lib().sfd_synthesize_noalloc(device, stream, ctypes.byref(params), ctypes.byref(exc), n_samples, ptr))
 
 
 # ------------------------------------------------------ dict marshalling
