@@ -54,9 +54,13 @@ FLOP_EXCITATION = 30.0    # per string-step with a hammer or bow (scalar solve +
 FLOP_RESPONSE_U = 10.0    # per transverse row for the unit-force response (nonlinear, forced)
 
 
-def algorithmic_flops(strings, grids) -> float:
+def algorithmic_flops(strings, grids, select=None) -> float:
+    """Algorithmic FLOPs of one synthesis of `strings` (optionally only the
+    indices in `select`)."""
     tot = 0.0
-    for d, (nt, nl) in zip(strings, grids):
+    for idx, (d, (nt, nl)) in enumerate(zip(strings, grids)):
+        if select is not None and idx not in select:
+            continue
         n_u = nt - 1
         linear = d["alpha"] == 1.0
         n_z = 0 if linear else max(nl - 1, 0)
@@ -65,6 +69,34 @@ def algorithmic_flops(strings, grids) -> float:
             per += FLOP_EXCITATION + (0.0 if linear else n_u * FLOP_RESPONSE_U)
         tot += per * (d["n_samples"] - 2)
     return tot
+
+
+KERNEL_SOURCES = ["sfd_kernel.cu", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_types.h"]
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2311_18505_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` on the default workload from the
+    committed ncu summary, or None when the summary is missing or was taken
+    on different kernel sources."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel}_dram_mixed256x2s.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_sources_sha256: ([0-9a-f]+)", txt)
+    mb = re.search(r"dram_bytes_per_launch: (\d+)", txt)
+    if not (mh and mb) or mh.group(1) != kernel_sources_hash():
+        return None
+    return int(mb.group(1))
 
 
 # ----------------------------------------------------------------- clocks
@@ -233,11 +265,12 @@ def run_ours(args, ws, rank, local):
         for h in hs:
             sfd.sfd_string_destroy(h)
 
-    grids = []   # grid sizes as the library derived them
+    grids, classes = [], []   # grid sizes and kernel classes as the library derived them
     for d in strings:
         h = sfd.string_from_dict(ctx, d)
         nt, nl, _, _ = sfd.sfd_string_info(h)
         grids.append((nt, nl))
+        classes.append(sfd.sfd_string_kernel_class(h))
         sfd.sfd_string_destroy(h)
     flops = algorithmic_flops(strings, grids)
     updates = sum(((nt - 1) + (0 if d["alpha"] == 1.0 else max(nl - 1, 0))) * (d["n_samples"] - 2)
@@ -253,6 +286,8 @@ def run_ours(args, ws, rank, local):
     batches = [make_batch() for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sfd.sfd_ctx_set_timing(ctx, True)
+    class_ms = [0.0] * sfd.SFD_KERNEL_CLASSES
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
@@ -264,9 +299,13 @@ def run_ours(args, ws, rank, local):
         sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
         ev[i][1].record(stream)
         launches += sfd.sfd_last_launch_count(ctx)
+        # per-class kernel times, recorded with events on each kernel's own stream
+        ms_k, _ = sfd.sfd_ctx_kernel_times(ctx)
+        class_ms = [a + b for a, b in zip(class_ms, ms_k)]
     torch.cuda.synchronize(dev)
     barrier(ws)
     clk = clocks.stop()
+    sfd.sfd_ctx_set_timing(ctx, False)
     times_ms = [a.elapsed_time(b) for a, b in ev]
     y = out[: min(total, 1 << 20)].float().cpu().numpy()
     finite = bool(np.all(np.isfinite(y)))
@@ -305,8 +344,14 @@ def run_ours(args, ws, rank, local):
     if rank != 0:
         return 0
     peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    avg_launch_s = sum(times_ms) / len(times_ms) / 1e3
-    achieved = flops / avg_launch_s / 1e12
+    # dominant kernel: the class kernel with the largest average launch time
+    dom = max(range(len(class_ms)), key=lambda k: class_ms[k])
+    dom_ms = class_ms[dom] / args.steps
+    dom_idx = {i for i, c in enumerate(classes) if c == dom}
+    achieved = algorithmic_flops(strings, grids, dom_idx) / (dom_ms / 1e3) / 1e12
+    class_names = ["synth_kernel_reg1", "synth_kernel_reg3", "synth_kernel_reg5", "synth_kernel_reg7",
+                   "synth_kernel_reg9", "synth_kernel_smem"]
+    default_workload = args.strings == 256 and args.seconds == 2.0 and ws == 1
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         sample = strings[: args.cpu_strings]
@@ -322,8 +367,13 @@ def run_ours(args, ws, rank, local):
                    "samples_per_step": total, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": "one persistent kernel per step, one warp per string"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(class_names[dom]) if default_workload else None,
+                     "kernel": class_names[dom], "kernel_ms": dom_ms, "kernel_strings": len(dom_idx),
+                     "class_ms": {class_names[k]: class_ms[k] / args.steps for k in range(len(class_ms))
+                                  if class_ms[k] > 0},
+                     "step_flops_total": flops,
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived, not measured)"},
         "grid_point_updates_per_s": ws * updates * args.steps / t_total,
         "realtime_factor": ws * total / FS * args.steps / t_total,
         "cpu_baseline": cpu,
@@ -348,9 +398,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-strings", type=int, default=64)
-    ap.add_argument("--cpu-samples", type=int, default=12000)
-    ap.add_argument("--ref-strings", type=int, default=32)
-    ap.add_argument("--ref-samples", type=int, default=4800)
+    ap.add_argument("--cpu-samples", type=int, default=36000)
+    ap.add_argument("--ref-strings", type=int, default=64)
+    ap.add_argument("--ref-samples", type=int, default=36000)
     args = ap.parse_args(argv)
     ws, rank, local = dist_setup(args.gpus)
     try:

@@ -176,6 +176,22 @@ sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, flo
 /* Number of kernel launches issued by the last batch/synthesize call. */
 int32_t sfd_last_launch_count(const sfd_ctx* ctx);
 
+/* Number of step-kernel classes: strings are grouped by transverse rows per
+ * lane (1, 3, 5, 7, 9 held in registers; more in shared memory) and each
+ * group runs as its own persistent kernel, concurrently with the others. */
+#define SFD_KERNEL_CLASSES 6
+
+/* Per-class kernel timing: when enabled, every launch records CUDA events
+ * around each class kernel on the stream it runs on; sfd_ctx_kernel_times
+ * waits for them and reports, for the last batch/synthesize call, each
+ * class's kernel time [ms] and job count (ms[SFD_KERNEL_CLASSES],
+ * n_jobs[SFD_KERNEL_CLASSES]; zeros for classes not launched). */
+sfd_status sfd_ctx_set_timing(sfd_ctx* ctx, int32_t enable);
+sfd_status sfd_ctx_kernel_times(sfd_ctx* ctx, float* ms, int32_t* n_jobs);
+
+/* Kernel class (0 .. SFD_KERNEL_CLASSES-1) a string runs in. */
+sfd_status sfd_string_kernel_class(const sfd_string* s, int32_t* cls);
+
 /* Cumulative bytes the library copied host->device and device->host on this
  * context (state uploads, job tables, outputs, status reads). */
 sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint64_t* d2h_total);

@@ -131,6 +131,9 @@ struct sfd_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side[kClasses] = {};      // one per kernel class, forked from `stream`
   cudaEvent_t fork = nullptr, join[kClasses] = {};
+  bool timing = false;                   // record per-class kernel times
+  cudaEvent_t t0[kClasses] = {}, t1[kClasses] = {};
+  int timed_jobs[kClasses] = {};         // jobs of each class in the last launch
   Pool pool;
   int sm_count = 0;
   size_t smem_optin = 0;
@@ -403,6 +406,7 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
     if (v >= 1 && v <= 4) wpc_all = v;
   }
   if (active > 1) SFD_CUDA(cudaEventRecord(c->fork, c->stream));
+  for (int k = 0; k < kClasses; ++k) c->timed_jobs[k] = 0;
   for (int k = 0; k < kClasses; ++k) {
     const int n_k = first[k + 1] - first[k];
     if (n_k == 0) continue;
@@ -418,8 +422,13 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
       st = c->side[k];
       SFD_CUDA(cudaStreamWaitEvent(st, c->fork, 0));
     }
+    if (c->timing) SFD_CUDA(cudaEventRecord(c->t0[k], st));
     cudaError_t e = kLaunch[k](c->d_jobs + first[k], n_k, c->d_counter + k, wf[k], wpc, n_ctas, st);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (c->timing) {
+      SFD_CUDA(cudaEventRecord(c->t1[k], st));
+      c->timed_jobs[k] = n_k;
+    }
     c->last_launches++;
     if (active > 1) {
       SFD_CUDA(cudaEventRecord(c->join[k], st));
@@ -496,7 +505,8 @@ sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes
   bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; k < kClasses && ok; ++k) {
     ok = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreate(&c->t0[k]) == cudaSuccess && cudaEventCreate(&c->t1[k]) == cudaSuccess;
   }
   if (!ok) {
     sfd_ctx_destroy(c);
@@ -513,6 +523,8 @@ void sfd_ctx_destroy(sfd_ctx* c) {
   for (int k = 0; k < kClasses; ++k) {
     if (c->side[k]) cudaStreamDestroy(c->side[k]);
     if (c->join[k]) cudaEventDestroy(c->join[k]);
+    if (c->t0[k]) cudaEventDestroy(c->t0[k]);
+    if (c->t1[k]) cudaEventDestroy(c->t1[k]);
   }
   if (c->fork) cudaEventDestroy(c->fork);
   c->pool.release();
@@ -529,6 +541,32 @@ sfd_status sfd_ctx_memory(const sfd_ctx* c, size_t* used, size_t* total) {
 }
 
 int32_t sfd_last_launch_count(const sfd_ctx* c) { return c ? c->last_launches : 0; }
+
+sfd_status sfd_ctx_set_timing(sfd_ctx* c, int32_t enable) {
+  if (!c) return fail(SFD_EINVAL, "ctx is NULL");
+  c->timing = enable != 0;
+  return SFD_OK;
+}
+
+sfd_status sfd_ctx_kernel_times(sfd_ctx* c, float* ms, int32_t* n_jobs) {
+  if (!c || !ms || !n_jobs) return fail(SFD_EINVAL, "NULL argument");
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  for (int k = 0; k < kClasses; ++k) {
+    ms[k] = 0.f;
+    n_jobs[k] = c->timing ? c->timed_jobs[k] : 0;
+    if (n_jobs[k] == 0) continue;
+    SFD_CUDA(cudaEventSynchronize(c->t1[k]));
+    SFD_CUDA(cudaEventElapsedTime(&ms[k], c->t0[k], c->t1[k]));
+  }
+  return SFD_OK;
+}
+
+sfd_status sfd_string_kernel_class(const sfd_string* s, int32_t* cls) {
+  if (!s || !cls) return fail(SFD_EINVAL, "NULL argument");
+  *cls = job_class(s->h);
+  return SFD_OK;
+}
 
 sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* c, uint64_t* h2d_total, uint64_t* d2h_total) {
   if (!c) return fail(SFD_EINVAL, "ctx is NULL");

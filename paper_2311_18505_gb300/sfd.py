@@ -89,6 +89,9 @@ def lib() -> ctypes.CDLL:
         "sfd_batch_destroy": (i32, [vp]),
         "sfd_last_launch_count": (i32, [vp]),
         "sfd_ctx_transfer_bytes": (i32, [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "sfd_ctx_set_timing": (i32, [vp, i32]),
+        "sfd_ctx_kernel_times": (i32, [vp, P(ctypes.c_float), P(i32)]),
+        "sfd_string_kernel_class": (i32, [vp, P(i32)]),
         "sfd_synthesize_noalloc": (i32, [ctypes.c_int, vp, P(sfd_string_params), P(sfd_excitation), i64, vp]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
@@ -258,6 +261,27 @@ def sfd_ctx_transfer_bytes(ctx: int) -> tuple[int, int]:
     a, b = ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().sfd_ctx_transfer_bytes(ctx, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+SFD_KERNEL_CLASSES = 6
+
+
+def sfd_ctx_set_timing(ctx: int, enable: bool) -> None:
+    _check(lib().sfd_ctx_set_timing(ctx, 1 if enable else 0))
+
+
+def sfd_ctx_kernel_times(ctx: int):
+    """(ms per class, jobs per class) of the last launch (timing enabled)."""
+    ms = (ctypes.c_float * SFD_KERNEL_CLASSES)()
+    nj = (ctypes.c_int32 * SFD_KERNEL_CLASSES)()
+    _check(lib().sfd_ctx_kernel_times(ctx, ms, nj))
+    return list(ms), list(nj)
+
+
+def sfd_string_kernel_class(s: int) -> int:
+    c = ctypes.c_int32()
+    _check(lib().sfd_string_kernel_class(s, ctypes.byref(c)))
+    return c.value
 
 
 def sfd_last_error() -> str:
