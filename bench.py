@@ -5,10 +5,15 @@ Workload (one "step"): 256 strings, 2 s at 48 kHz each (96,000 samples),
 f0 log-uniform 40-1000 Hz, kappa U[0.5,3], alpha U[1,10], sigma0 U[0.1,2],
 sigma1 U[1e-6,1e-4], excitation uniform over pluck / hammer / bow (seed 2),
 synthesized from the initial state by one launch of the persistent step
-kernel.  Every step starts from freshly created strings (inputs resident in
-device memory before the timed region); L2 is flushed between timed steps.
+kernel per class.  Every step starts from freshly created strings (inputs
+resident in device memory before the timed region); L2 is flushed between
+timed steps.  `--workload modulated` times the batching workload instead:
+4096 strings of uneven N, f0 log-uniform 30-2000 Hz with vibrato or
+glissando, 4 s each, warps per CTA autotuned once, each step one CUDA-graph
+replay of the prepared launch.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload mixed|modulated]
 
 Under torchrun each rank synthesizes its own 256-string batch (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -206,12 +211,22 @@ def cpu_oracle_rate(strings, n_samples: int, threads: int = 0):
 
 WORKLOAD_NAME = ("256 strings x 2 s at 48 kHz: f0 log-U[40,1000] Hz, kappa U[0.5,3], alpha U[1,10], "
                  "sigma0 U[0.1,2], sigma1 U[1e-6,1e-4], pluck/hammer/bow uniform (seed 2)")
+WORKLOAD_MODULATED = ("4096 strings x 4 s at 48 kHz, uneven N: f0 log-U[30,2000] Hz, half vibrato (5-7 Hz, "
+                      "+-20 cents), half glissando (+-1 octave), parameters and excitations as the mixed batch "
+                      "(seed 3); one CUDA-graph replay per step, autotuned warps per CTA")
+
+
+def make_workload(args, rank):
+    if args.workload == "modulated":
+        return W.batch_modulated(args.strings or 4096, seconds=args.seconds or 4.0, seed=3 + 1000 * rank), \
+            WORKLOAD_MODULATED
+    return W.batch_mixed(args.strings or 256, seconds=args.seconds or 2.0, seed=2 + 1000 * rank), WORKLOAD_NAME
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    strings = W.batch_mixed(args.strings, seconds=args.seconds, seed=2)
+    strings, workload_name = make_workload(args, 0)
     sample = strings[: args.ref_strings]
     n = args.ref_samples
     for _ in range(args.warmup):
@@ -227,7 +242,7 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "reference": "FP64 CPU oracle (OpenMP)"},
+        "data": "synthetic", "config": {"workload": workload_name, "reference": "FP64 CPU oracle (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -245,9 +260,11 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 1 << 30)
-    strings = W.batch_mixed(args.strings, seconds=args.seconds, seed=2 + 1000 * rank)
+    stream = torch.cuda.Stream(dev)            # the context's stream (also the capture stream)
+    torch.cuda.set_stream(stream)
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 4 << 30)
+    strings, workload_name = make_workload(args, rank)
+    graphed = args.workload == "modulated"
     ns = np.array([d["n_samples"] for d in strings], dtype=np.int64)
     offs = np.zeros(len(ns), dtype=np.int64)
     offs[1:] = np.cumsum(ns)[:-1]
@@ -276,32 +293,61 @@ def run_ours(args, ws, rank, local):
     updates = sum(((nt - 1) + (0 if d["alpha"] == 1.0 else max(nl - 1, 0))) * (d["n_samples"] - 2)
                   for d, (nt, nl) in zip(strings, grids))
 
+    wpc = 0
+    if not graphed:
+        sfd.sfd_ctx_set_timing(ctx, True)
+    if graphed:   # autotune warps per CTA once, on throwaway copies
+        hb = make_batch()
+        wpc = sfd.sfd_batch_autotune(hb[1], 2048)
+        free_batch(hb)
+
+    def prepared_batch():
+        """A fresh batch, its job table uploaded and (modulated workload) its
+        launch captured as a CUDA graph."""
+        hb = make_batch()
+        if wpc:
+            sfd.sfd_batch_set_warps_per_cta(hb[1], wpc)
+        g = None
+        if graphed:
+            sfd.sfd_batch_prepare(hb[1], ns, out, offs)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                sfd.sfd_batch_launch(hb[1])
+        return hb, g
+
+    def run_step(hb, g):
+        if g is not None:
+            g.replay()
+        else:
+            sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+
     # warm-up
     for _ in range(args.warmup):
-        hb = make_batch()
-        sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+        hb, g = prepared_batch()
+        run_step(hb, g)
         torch.cuda.synchronize(dev)
+        del g
         free_batch(hb)
-    # timed: inputs for every step created before the region
-    batches = [make_batch() for _ in range(args.steps)]
+    # timed: inputs for every step created (and captured) before the region
+    batches = [prepared_batch() for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sfd.sfd_ctx_set_timing(ctx, True)
     class_ms = [0.0] * sfd.SFD_KERNEL_CLASSES
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
     torch.cuda.synchronize(dev)
     launches = 0
-    for i, hb in enumerate(batches):
+    for i, (hb, g) in enumerate(batches):
         flush.zero_()
         ev[i][0].record(stream)
-        sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+        run_step(hb, g)
         ev[i][1].record(stream)
-        launches += sfd.sfd_last_launch_count(ctx)
-        # per-class kernel times, recorded with events on each kernel's own stream
-        ms_k, _ = sfd.sfd_ctx_kernel_times(ctx)
-        class_ms = [a + b for a, b in zip(class_ms, ms_k)]
+        launches += len(set(classes)) if g is not None else sfd.sfd_last_launch_count(ctx)
+        if g is None:
+            # per-class kernel times, recorded with events on each kernel's own stream
+            ms_k, _ = sfd.sfd_ctx_kernel_times(ctx)
+            class_ms = [a + b for a, b in zip(class_ms, ms_k)]
     torch.cuda.synchronize(dev)
     barrier(ws)
     clk = clocks.stop()
@@ -309,7 +355,8 @@ def run_ours(args, ws, rank, local):
     times_ms = [a.elapsed_time(b) for a, b in ev]
     y = out[: min(total, 1 << 20)].float().cpu().numpy()
     finite = bool(np.all(np.isfinite(y)))
-    for hb in batches:
+    for hb, g in batches:
+        del g
         free_batch(hb)
     t_total = max_over_ranks(ws, sum(times_ms) / 1e3)
     value = ws * total * args.steps / t_total
@@ -345,13 +392,19 @@ def run_ours(args, ws, rank, local):
         return 0
     peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     # dominant kernel: the class kernel with the largest average launch time
-    dom = max(range(len(class_ms)), key=lambda k: class_ms[k])
-    dom_ms = class_ms[dom] / args.steps
-    dom_idx = {i for i, c in enumerate(classes) if c == dom}
+    if sum(class_ms) > 0:
+        dom = max(range(len(class_ms)), key=lambda k: class_ms[k])
+        dom_ms = class_ms[dom] / args.steps
+        dom_idx = {i for i, c in enumerate(classes) if c == dom}
+    else:   # graph replays: the concurrent class kernels timed together
+        dom = 0
+        dom_ms = sum(times_ms) / len(times_ms)
+        dom_idx = set(range(len(strings)))
     achieved = algorithmic_flops(strings, grids, dom_idx) / (dom_ms / 1e3) / 1e12
     class_names = ["synth_kernel_reg1", "synth_kernel_reg3", "synth_kernel_reg5", "synth_kernel_reg7",
                    "synth_kernel_reg9", "synth_kernel_smem"]
-    default_workload = args.strings == 256 and args.seconds == 2.0 and ws == 1
+    default_workload = args.workload == "mixed" and len(strings) == 256 and ws == 1 and \
+        strings[0]["n_samples"] == 96000
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         sample = strings[: args.cpu_strings]
@@ -363,13 +416,18 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "strings": args.strings, "seconds": args.seconds, "fs": FS,
+        "config": {"workload": workload_name, "strings": len(strings),
+                   "seconds": float(strings[0]["n_samples"] / FS), "fs": FS,
                    "samples_per_step": total, "l2": "flushed between timed steps (256 MiB write)",
-                   "launch": "one persistent kernel per step, one warp per string"},
+                   "launch": ("one CUDA-graph replay per step (concurrent class kernels), warps per CTA "
+                              f"autotuned to {wpc}") if graphed else
+                             "one persistent kernel per class per step, one warp per string"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": measured_traffic(class_names[dom]) if default_workload else None,
-                     "kernel": class_names[dom], "kernel_ms": dom_ms, "kernel_strings": len(dom_idx),
+                     "kernel": class_names[dom] if sum(class_ms) > 0 else
+                               "synth_kernel_* (all classes, concurrent in one graph replay)",
+                     "kernel_ms": dom_ms, "kernel_strings": len(dom_idx),
                      "class_ms": {class_names[k]: class_ms[k] / args.steps for k in range(len(class_ms))
                                   if class_ms[k] > 0},
                      "step_flops_total": flops,
@@ -392,8 +450,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--strings", type=int, default=256)
-    ap.add_argument("--seconds", type=float, default=2.0)
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated"])
+    ap.add_argument("--strings", type=int, default=0)
+    ap.add_argument("--seconds", type=float, default=0.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -196,6 +196,28 @@ sfd_status sfd_string_kernel_class(const sfd_string* s, int32_t* cls);
  * context (state uploads, job tables, outputs, status reads). */
 sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint64_t* d2h_total);
 
+/* Warps per CTA for this batch's launches: 1..4, or 0 (default) for
+ * automatic (jobs / SMs, clamped).  Warps of one CTA run on different SM
+ * sub-partitions, so this sets how many strings share an SM. */
+sfd_status sfd_batch_set_warps_per_cta(sfd_batch* b, int32_t warps_per_cta);
+
+/* Choose warps per CTA by measurement: runs probe_samples samples of every
+ * string for each candidate (1, 2, 4) on throwaway copies of the strings'
+ * current state (the batch's strings are not advanced), keeps the fastest
+ * for the batch and returns it in *best (may be NULL). */
+sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best_warps_per_cta);
+
+/* Split form of sfd_batch_synthesize for CUDA-graph capture.  prepare
+ * uploads the batch's job table (string i advances n_samples[i] samples into
+ * out_device + out_offsets[i]) and waits for it; launch then only enqueues
+ * the kernels on the context stream (no host<->device copies, no
+ * allocation), so it may be captured into a CUDA graph and replayed: every
+ * launch or replay advances each string by its n_samples and overwrites the
+ * same output ranges.  Per-class kernel timing is skipped while the
+ * context stream is capturing. */
+sfd_status sfd_batch_prepare(sfd_batch* b, const int64_t* n_samples, float* out_device, const int64_t* out_offsets);
+sfd_status sfd_batch_launch(sfd_batch* b);
+
 sfd_status sfd_batch_destroy(sfd_batch* b);
 
 /* Excitation of a string for sfd_synthesize_noalloc (same meaning and units

@@ -164,6 +164,11 @@ struct sfd_string {
 struct sfd_batch {
   sfd_ctx* ctx = nullptr;
   std::vector<sfd_string*> strings;
+  int wpc = 0;                 // warps per CTA (0: automatic)
+  // prepared launch (sfd_batch_prepare / sfd_batch_launch)
+  void* plan = nullptr;        // Plan*
+  char* d_jobs = nullptr;      // pool block holding the plan's job table
+  size_t d_jobs_bytes = 0;
 };
 
 namespace {
@@ -228,6 +233,52 @@ void point_weights(int n_t, double x, int32_t* node, float* w) {
 double n_l_sq(const sfd_string* s) { return static_cast<double>(s->n_l) * s->n_l; }
 
 // Coefficients of the acceleration-form update (see sfd_kernel.cu), FP64 -> FP32.
+// Best rational approximation num/den of x > 0 with num, den < 2^24
+// (continued-fraction convergents and the last semiconvergent).
+static void rational24(double x, double* num, double* den) {
+  const double lim = 16777216.0;   // 2^24
+  double p0 = 0, q0 = 1, p1 = 1, q1 = 0, y = x;
+  double bp = std::max(1.0, std::min(lim - 1, std::round(x))), bq = 1;
+  auto consider = [&](double p, double q) {
+    if (p > 0 && q > 0 && p < lim && q < lim && std::fabs(p / q - x) < std::fabs(bp / bq - x)) { bp = p; bq = q; }
+  };
+  for (int it = 0; it < 64; ++it) {
+    const double a = std::floor(y);
+    const double p2 = a * p1 + p0, q2 = a * q1 + q0;
+    if (p2 >= lim || q2 >= lim) {
+      double t = std::floor((lim - 1 - p0) / p1);
+      if (q1 > 0) t = std::min(t, std::floor((lim - 1 - q0) / q1));
+      if (t >= 1) consider(t * p1 + p0, t * q1 + q0);
+      break;
+    }
+    consider(p2, q2);
+    p0 = p1; q0 = q1; p1 = p2; q1 = q2;
+    const double f = y - a;
+    if (f < 1e-300) break;
+    y = 1.0 / f;
+  }
+  *num = bp;
+  *den = bq;
+}
+
+// Scale beta of the transverse equation such that beta dg and beta og are
+// floats: with dg/og ~ P/Q (P, Q < 2^24), dg' = P 2^e and og' = Q 2^e are
+// exact, and beta = og'/og is within a factor 2^(1/2) of 1.  The ratio
+// dg'/og' = P/Q matches dg/og to ~1e-14.  Falls back to plain rounding when
+// og is zero or the ratio is out of range.
+static void exact_matrix_scale(double dg, double og, float* dg_s, float* og_s) {
+  *dg_s = static_cast<float>(dg);
+  *og_s = static_cast<float>(og);
+  if (!(og != 0.0) || !(dg > 0.0)) return;
+  const double r = dg / std::fabs(og);
+  if (!(r > 1e-6 && r < 1e6)) return;
+  double P, Q;
+  rational24(r, &P, &Q);
+  const int e = static_cast<int>(std::lround(std::log2(std::fabs(og) / Q)));
+  *dg_s = static_cast<float>(std::ldexp(P, e));
+  *og_s = static_cast<float>(std::copysign(std::ldexp(Q, e), og));
+}
+
 void fill_desc(sfd_string* s) {
   const sfd_string_params& p = s->p;
   Desc& D = s->h;
@@ -248,21 +299,39 @@ void fill_desc(sfd_string* s) {
     D.z_jacobi = (2.0 * s1l / (1.0 + p.sigma0 * k + 2.0 * s1l) <= 0.01) ? 1 : 0;
   }
   D.boundary = p.boundary;
-  D.th = static_cast<float>(p.theta);
-  D.tho = static_cast<float>(0.5 * (1.0 - p.theta));
-  D.s0 = static_cast<float>(p.sigma0 * k);
-  D.s1 = static_cast<float>(p.sigma1 * k / (ht * ht));
+  const double s0 = p.sigma0 * k, s1 = p.sigma1 * k / (ht * ht);
+  D.dg = static_cast<float>(p.theta + s0 + 2.0 * s1);
+  D.og = static_cast<float>(0.5 * (1.0 - p.theta) - s1);
+  // A constant matrix entry rounded to FP32 is a perturbation of the scheme
+  // that lasts the whole run: an error of ~3e-8 in dg or og shifts mode
+  // frequencies by about as much, a phase error growing with f0 * t that
+  // reaches the 1e-4 tolerance over 0.25 s near 2 kHz.  Multiplying the
+  // transverse equation by beta (exact_matrix_scale) makes dg and og exact;
+  // every other transverse coefficient takes the same factor, computed from
+  // the stored entries so that the rows sum to exactly beta (1 + s0).
+  exact_matrix_scale(p.theta + s0 + 2.0 * s1, 0.5 * (1.0 - p.theta) - s1, &D.dg, &D.og);
+  const double rho = (static_cast<double>(D.dg) + 2.0 * static_cast<double>(D.og)) / (1.0 + s0);
+  D.s0 = static_cast<float>(s0);
+  D.s0u = static_cast<float>(s0 * rho);
+  D.s1 = static_cast<float>(s1 * rho);
   D.s1l = static_cast<float>(p.sigma1 * k / (hl * hl));
-  D.lam2 = static_cast<float>(g * g * k * k / (ht * ht));
-  D.mu2 = static_cast<float>(p.kappa * p.kappa * k * k / (ht * ht * ht * ht));
+  const double lam2 = g * g * k * k / (ht * ht) * rho;   // carried as a float pair
+  D.lam2 = static_cast<float>(lam2);
+  D.lam2_lo = static_cast<float>(lam2 - static_cast<double>(D.lam2));
+  D.mu2 = static_cast<float>(p.kappa * p.kappa * k * k / (ht * ht * ht * ht) * rho);
   D.lam2l = static_cast<float>(g * g * p.alpha * p.alpha * k * k / (hl * hl));
   const double phi = 0.5 * g * g * (p.alpha * p.alpha - 1.0);   // phi' of Eq. 4
-  D.ca = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht * ht));
-  D.cb = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht));
+  D.ca = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht * ht) * rho);
+  D.cb = static_cast<float>(phi * k * k / (2.0 * ht * ht * ht) * rho);
   D.cz = static_cast<float>(phi * k * k / (2.0 * ht * ht * hl));
   D.out_scale = static_cast<float>(p.length_m);
   point_weights(s->n_t, p.pickup_pos, &D.o_node, &D.o_w);
-  D.jscale = static_cast<float>(s->n_t);
+  D.jscale = static_cast<float>(s->n_t * rho);
+  // The FP32 factorisation of the transverse matrix is itself a lasting
+  // perturbation of the same size.  Strings of at most 31 unknowns (f0
+  // above ~450 Hz, the most cycles in a given time) correct each solve once
+  // against the exact matrix.
+  D.refine = D.m_u == 1 ? 1 : 0;
   D.k = static_cast<float>(k);
   D.k2 = static_cast<float>(k * k);
   D.exc = s->exc;
@@ -361,14 +430,18 @@ using Launcher = cudaError_t (*)(const Job*, int, int*, int, int, int, cudaStrea
 const Launcher kLaunch[kClasses] = {launch_synth_reg1, launch_synth_reg3, launch_synth_reg5,
                                     launch_synth_reg7, launch_synth_reg9, launch_synth_smem};
 
-// Queue the persistent kernels for `jobs` on the context stream: jobs are
-// grouped by kernel class (transverse rows per lane), each class sorted
-// longest first (the order its work queue hands them out), and the classes
-// run concurrently on side streams forked from and joined back to the
-// context stream.
-sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners) {
-  c->last_launches = 0;
-  if (jobs.empty()) return SFD_OK;
+// A launch plan: jobs grouped by kernel class (transverse rows per lane),
+// each class sorted longest first (the order its work queue hands them
+// out), with each class's shared-memory need and the warps per CTA.
+struct Plan {
+  std::vector<Job> jobs;
+  int first[kClasses + 1] = {};
+  int wf[kClasses] = {};
+  int wpc = 1;
+};
+
+sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners,
+                     int wpc_override, Plan& P) {
   const int nj = static_cast<int>(jobs.size());
   std::vector<int> order(nj), cls(nj);
   std::vector<double> cost(nj);
@@ -381,40 +454,51 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
     if (cls[a] != cls[b]) return cls[a] < cls[b];
     return cost[a] > cost[b];
   });
-  std::vector<Job> sorted(nj);
-  int first[kClasses + 1] = {}, wf[kClasses] = {};
-  for (int i = 0; i < nj; ++i) sorted[i] = jobs[order[i]];
+  P.jobs.assign(nj, Job{});
+  for (int k = 0; k <= kClasses; ++k) P.first[k] = 0;
+  for (int k = 0; k < kClasses; ++k) P.wf[k] = 0;
+  for (int i = 0; i < nj; ++i) P.jobs[i] = jobs[order[i]];
   for (int i = 0; i < nj; ++i) {
     const int k = cls[order[i]];
-    first[k + 1]++;
+    P.first[k + 1]++;
     const Desc& D = owners[order[i]]->h;
-    wf[k] = std::max(wf[k], warp_smem_floats(D.m_u, D.m_z, D.z_jacobi));
+    P.wf[k] = std::max(P.wf[k], warp_smem_floats(D.m_u, D.m_z, D.z_jacobi));
   }
-  for (int k = 0; k < kClasses; ++k) first[k + 1] += first[k];
-  sfd_status rc = ensure_jobs(c, nj);
-  if (rc) return rc;
-  SFD_CUDA(h2d(c, c->d_jobs, sorted.data(), sizeof(Job) * nj));
-  int active = 0;
-  for (int k = 0; k < kClasses; ++k) active += first[k + 1] > first[k];
+  for (int k = 0; k < kClasses; ++k) P.first[k + 1] += P.first[k];
+  for (int k = 0; k < kClasses; ++k) {
+    if (static_cast<size_t>(P.wf[k]) * sizeof(float) > c->smem_optin)
+      return fail(SFD_EINVAL, "string too large for one warp's shared memory");
+  }
   // warps per CTA: ceil(jobs / SMs), 1..4.  Warps of one CTA sit on
   // different SM sub-partitions, so pairing jobs in a CTA keeps each string
   // on a scheduler of its own (measured on the 256-string batch: 2 warps per
   // CTA 27.3 M samples/s vs 19.9 M with single-warp CTAs).
-  int wpc_all = std::max(1, std::min(4, (nj + c->sm_count - 1) / c->sm_count));
+  int wpc = std::max(1, std::min(4, (nj + c->sm_count - 1) / std::max(c->sm_count, 1)));
   if (const char* env = getenv("SFD_WARPS_PER_CTA")) {
     const int v = atoi(env);
-    if (v >= 1 && v <= 4) wpc_all = v;
+    if (v >= 1 && v <= 4) wpc = v;
   }
+  if (wpc_override >= 1 && wpc_override <= 4) wpc = wpc_override;
+  P.wpc = wpc;
+  return SFD_OK;
+}
+
+// Issue the plan's kernels on the context stream (job table already in
+// device memory at d_jobs).  Classes run concurrently on side streams forked
+// from and joined back to the context stream.  No host<->device copies, so
+// this can be captured into a CUDA graph.
+sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
+  c->last_launches = 0;
+  int active = 0;
+  for (int k = 0; k < kClasses; ++k) active += P.first[k + 1] > P.first[k];
+  if (active == 0) return SFD_OK;
   if (active > 1) SFD_CUDA(cudaEventRecord(c->fork, c->stream));
   for (int k = 0; k < kClasses; ++k) c->timed_jobs[k] = 0;
   for (int k = 0; k < kClasses; ++k) {
-    const int n_k = first[k + 1] - first[k];
+    const int n_k = P.first[k + 1] - P.first[k];
     if (n_k == 0) continue;
-    const size_t wbytes = static_cast<size_t>(wf[k]) * sizeof(float);
-    if (wbytes > c->smem_optin)
-      return fail(SFD_EINVAL, "string too large for one warp's shared memory (%zu > %zu bytes)", wbytes,
-                  c->smem_optin);
-    int wpc = static_cast<int>(std::min<size_t>(static_cast<size_t>(wpc_all), c->smem_optin / wbytes));
+    const size_t wbytes = static_cast<size_t>(P.wf[k]) * sizeof(float);
+    int wpc = static_cast<int>(std::min<size_t>(static_cast<size_t>(P.wpc), c->smem_optin / wbytes));
     wpc = std::max(1, wpc);
     const int n_ctas = (n_k + wpc - 1) / wpc;
     cudaStream_t st = c->stream;
@@ -423,7 +507,7 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
       SFD_CUDA(cudaStreamWaitEvent(st, c->fork, 0));
     }
     if (c->timing) SFD_CUDA(cudaEventRecord(c->t0[k], st));
-    cudaError_t e = kLaunch[k](c->d_jobs + first[k], n_k, c->d_counter + k, wf[k], wpc, n_ctas, st);
+    cudaError_t e = kLaunch[k](d_jobs + P.first[k], n_k, c->d_counter + k, P.wf[k], wpc, n_ctas, st);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     if (c->timing) {
       SFD_CUDA(cudaEventRecord(c->t1[k], st));
@@ -436,6 +520,21 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
     }
   }
   return SFD_OK;
+}
+
+// Queue the persistent kernels for `jobs` on the context stream (job table
+// uploaded into the context's table).
+sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners,
+                       int wpc_override = 0) {
+  c->last_launches = 0;
+  if (jobs.empty()) return SFD_OK;
+  Plan P;
+  sfd_status rc = make_plan(c, jobs, owners, wpc_override, P);
+  if (rc) return rc;
+  rc = ensure_jobs(c, static_cast<int>(P.jobs.size()));
+  if (rc) return rc;
+  SFD_CUDA(h2d(c, c->d_jobs, P.jobs.data(), sizeof(Job) * P.jobs.size()));
+  return issue_plan(c, P, c->d_jobs);
 }
 
 sfd_status read_status(const sfd_string* s, Scalars* out) {
@@ -856,7 +955,7 @@ static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_d
     jobs.push_back(Job{b->strings[i]->d_desc, out_device + offsets[i], n_samples[i]});
     owners.push_back(b->strings[i]);
   }
-  rc = launch_jobs(c, jobs, owners);
+  rc = launch_jobs(c, jobs, owners, b->wpc);
   for (auto* s : b->strings) s->started = true;
   if (rc) return rc;
   if (per_string_status) {
@@ -904,9 +1003,146 @@ sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, flo
   return rc;
 }
 
+sfd_status sfd_batch_set_warps_per_cta(sfd_batch* b, int32_t warps_per_cta) {
+  if (!b) return fail(SFD_EINVAL, "batch is NULL");
+  if (warps_per_cta < 0 || warps_per_cta > 4) return fail(SFD_EINVAL, "warps per CTA must be 0 (automatic) or 1..4");
+  b->wpc = warps_per_cta;
+  return SFD_OK;
+}
+
+sfd_status sfd_batch_prepare(sfd_batch* b, const int64_t* n_samples, float* out_device, const int64_t* out_offsets) {
+  if (!b || !n_samples || !out_device || !out_offsets) return fail(SFD_EINVAL, "NULL argument");
+  sfd_ctx* c = b->ctx;
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  std::vector<Job> jobs;
+  std::vector<const sfd_string*> owners;
+  for (size_t i = 0; i < b->strings.size(); ++i) {
+    if (n_samples[i] < 0) return fail(SFD_EINVAL, "n_samples[%zu] < 0", i);
+    if (n_samples[i] == 0) continue;
+    jobs.push_back(Job{b->strings[i]->d_desc, out_device + out_offsets[i], n_samples[i]});
+    owners.push_back(b->strings[i]);
+  }
+  Plan* P = b->plan ? static_cast<Plan*>(b->plan) : new (std::nothrow) Plan();
+  if (!P) return fail(SFD_ENOMEM, "host allocation failed");
+  b->plan = P;
+  if ((rc = make_plan(c, jobs, owners, b->wpc, *P))) return rc;
+  const size_t bytes = std::max<size_t>(sizeof(Job) * P->jobs.size(), sizeof(Job));
+  if (bytes > b->d_jobs_bytes) {
+    if (b->d_jobs) c->pool.dealloc(b->d_jobs);
+    b->d_jobs = c->pool.alloc(bytes);
+    b->d_jobs_bytes = b->d_jobs ? bytes : 0;
+    if (!b->d_jobs) return fail(SFD_ENOMEM, "device pool exhausted for the job table");
+  }
+  if (!P->jobs.empty()) SFD_CUDA(h2d(c, b->d_jobs, P->jobs.data(), sizeof(Job) * P->jobs.size()));
+  SFD_CUDA(cudaStreamSynchronize(c->stream));
+  return SFD_OK;
+}
+
+sfd_status sfd_batch_launch(sfd_batch* b) {
+  if (!b) return fail(SFD_EINVAL, "batch is NULL");
+  if (!b->plan) return fail(SFD_ESTATE, "sfd_batch_prepare must come first");
+  sfd_ctx* c = b->ctx;
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  for (auto* s : b->strings) s->started = true;
+  // per-class timing events cannot be read back from a graph: off while capturing
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SFD_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+  const bool timing = c->timing;
+  if (cap != cudaStreamCaptureStatusNone) c->timing = false;
+  rc = issue_plan(c, *static_cast<Plan*>(b->plan), reinterpret_cast<const Job*>(b->d_jobs));
+  c->timing = timing;
+  return rc;
+}
+
+// A string with the same parameters, excitation and current state (device
+// copy of the state block); used to probe launch settings without touching
+// the original.
+static sfd_status clone_string(const sfd_string* s, sfd_string** out) {
+  sfd_ctx* c = s->ctx;
+  sfd_string* t = new (std::nothrow) sfd_string(*s);
+  if (!t) return fail(SFD_ENOMEM, "host allocation failed");
+  t->batch_refs = 0;
+  t->block = c->pool.alloc(block_bytes(t->h));
+  if (!t->block) {
+    delete t;
+    return fail(SFD_ENOMEM, "device pool exhausted");
+  }
+  carve(t);
+  SFD_CUDA(h2d(c, t->d_desc, &t->h, sizeof(Desc)));
+  const size_t nz = t->h.n_z > 0 ? t->h.n_z : 1;
+  struct { void* d; const void* s; size_t n; } cp[] = {
+      {t->d_sc, s->d_sc, sizeof(Scalars)},      {t->h.u, s->h.u, sizeof(float) * t->h.n_u},
+      {t->h.du, s->h.du, sizeof(float) * t->h.n_u}, {t->h.z, s->h.z, sizeof(float) * nz},
+      {t->h.dz, s->h.dz, sizeof(float) * nz},    {t->h.xz, s->h.xz, sizeof(float) * nz},
+      {t->h.az, s->h.az, sizeof(float) * nz}};
+  for (auto& x : cp) SFD_CUDA(cudaMemcpyAsync(x.d, x.s, x.n, cudaMemcpyDeviceToDevice, c->stream));
+  *out = t;
+  return SFD_OK;
+}
+
+sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best_warps_per_cta) {
+  if (!b || probe_samples <= 0) return fail(SFD_EINVAL, "bad autotune arguments");
+  sfd_ctx* c = b->ctx;
+  sfd_status rc = set_device(c);
+  if (rc) return rc;
+  const size_t n = b->strings.size();
+  if (n == 0) return fail(SFD_EINVAL, "empty batch");
+  char* dout = c->pool.alloc(sizeof(float) * probe_samples * n);
+  if (!dout) return fail(SFD_ENOMEM, "device pool exhausted for the probe output");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  int best = 0;
+  const int candidates[3] = {1, 2, 4};
+  for (int ci = 0; ci < 3 && rc == SFD_OK; ++ci) {
+    // fresh clones of the current state for every candidate
+    std::vector<sfd_string*> cl;
+    for (size_t i = 0; i < n && rc == SFD_OK; ++i) {
+      sfd_string* t = nullptr;
+      rc = clone_string(b->strings[i], &t);
+      if (t) cl.push_back(t);
+    }
+    if (rc == SFD_OK) {
+      std::vector<Job> jobs;
+      std::vector<const sfd_string*> owners;
+      for (size_t i = 0; i < n; ++i) {
+        jobs.push_back(Job{cl[i]->d_desc, reinterpret_cast<float*>(dout) + i * probe_samples, probe_samples});
+        owners.push_back(cl[i]);
+      }
+      const bool timing = c->timing;
+      c->timing = false;
+      cudaEventRecord(e0, c->stream);
+      rc = launch_jobs(c, jobs, owners, candidates[ci]);
+      cudaEventRecord(e1, c->stream);
+      c->timing = timing;
+      if (rc == SFD_OK) {
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+        else if (best == 0 || ms < best_ms) { best_ms = ms; best = candidates[ci]; }
+      }
+    }
+    cudaStreamSynchronize(c->stream);
+    for (auto* t : cl) { c->pool.dealloc(t->block); delete t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->pool.dealloc(dout);
+  if (rc) return rc;
+  b->wpc = best;
+  if (best_warps_per_cta) *best_warps_per_cta = best;
+  return SFD_OK;
+}
+
 sfd_status sfd_batch_destroy(sfd_batch* b) {
   if (!b) return SFD_OK;
   for (auto* s : b->strings) s->batch_refs--;
+  if (b->d_jobs) b->ctx->pool.dealloc(b->d_jobs);
+  delete static_cast<Plan*>(b->plan);
   delete b;
   return SFD_OK;
 }

@@ -215,8 +215,8 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   const bool zjac = Dp->z_jacobi != 0;
   const int exc = Dp->exc;
   const int RU = kWarp * MU + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
-  const float th = Dp->th, tho = Dp->tho, s0 = Dp->s0, s1 = Dp->s1, s1l = Dp->s1l;
-  const float lam2_0 = Dp->lam2, mu2 = Dp->mu2, lam2l_0 = Dp->lam2l;
+  const float dg = Dp->dg, og = Dp->og, s0 = Dp->s0, s0u = Dp->s0u, s1 = Dp->s1, s1l = Dp->s1l;
+  const float lam2_0 = Dp->lam2, mu2 = Dp->mu2, lam2l_0 = Dp->lam2l, lam2lo_0 = Dp->lam2_lo;
   const float ca_0 = Dp->ca, cb_0 = Dp->cb, cz_0 = Dp->cz;
   const float bsgn = Dp->boundary == 1 ? -1.f : 1.f;
   const int mod_kind = Dp->mod_kind;
@@ -385,16 +385,22 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     tri_factor(SUBZ, INVZ, CPZ, ALZ, FFZ, GGZ, m_z, lane, rdz);
   }
   float SB[MU], IV[MU], CPr[MU], FFr[MU], GGr[MU];
+  // unfactored diagonal and superdiagonal, kept for the refinement residual
+  // (single-row lanes only: the strings that refine have at most 31 rows)
+  float DG0[MU], CP0[MU];
+  const bool refine = MU == 1 && Dp->refine != 0;
 #pragma unroll
   for (int r = 0; r < MU; ++r) {
     const int i = ub + r;
     if (i < n_u) {
-      SB[r] = i > 0 ? tho - s1 : 0.f;
-      IV[r] = th + s0 + 2.f * s1;
-      CPr[r] = i < n_u - 1 ? tho - s1 : 0.f;
+      SB[r] = i > 0 ? og : 0.f;
+      IV[r] = dg;
+      CPr[r] = i < n_u - 1 ? og : 0.f;
     } else {
       SB[r] = 0.f; IV[r] = 1.f; CPr[r] = 0.f;
     }
+    DG0[r] = IV[r];
+    CP0[r] = CPr[r];
   }
   const bool forced = exc != kPluck;
   const int en = Dp->e_node;
@@ -421,6 +427,20 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   }
   __syncwarp();
 
+  // One step of iterative refinement of the transverse solve A x = b: the
+  // residual against the unfactored entries (exact floats for a linear
+  // string) is solved with the same factors and added, which removes the
+  // lasting error of the FP32 factorisation from the solution.
+  auto refine_solve = [&](const float (&b)[MU], float (&x)[MU]) {
+    float xe[MU + 2], rr[MU];
+    extend1<MU>(x, xe, lane);
+#pragma unroll
+    for (int r = 0; r < MU; ++r) rr[r] = b[r] - (SB[r] * xe[r] + DG0[r] * xe[r + 1] + CP0[r] * xe[r + 2]);
+    tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, rr, rr, lane, rdu);
+#pragma unroll
+    for (int r = 0; r < MU; ++r) x[r] += rr[r];
+  };
+
   const int on = Dp->o_node;
   const float ow = Dp->o_w, oscale = Dp->out_scale;
   const int64_t j_end = jnext + job.n_samples;
@@ -440,6 +460,8 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         rm = exp2f(static_cast<float>(mod_inc * static_cast<double>(n)));
       }
       const float lam2 = lam2_0 * rm, lam2l = lam2l_0 * rm;
+      // low part of lam2_0 * rm (exact product residual plus the stored low part)
+      const float lam2_lo = fmaf(lam2_0, rm, -lam2) + lam2lo_0 * rm;
       const float ca = ca_0 * rm, cb = cb_0 * rm, cz = cz_0 * rm;
 
       float eta = 0.f, k2G = 0.f, FB = 0.f;
@@ -481,7 +503,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         if (i == n_u - 1) d4 += bsgn * u0;
         const float du0 = DUe[r + 1];
         const float d2du = (DUe[r + 2] - du0) - (du0 - DUe[r]);
-        float rhs = lam2 * d2 - mu2 * d4 - 2.f * s0 * du0 + 2.f * s1 * d2du;
+        float rhs = fmaf(lam2, d2, lam2_lo * d2) - mu2 * d4 - 2.f * s0u * du0 + 2.f * s1 * d2du;
         if (!linear) {
           const float gl2 = gl * gl, gr2 = gr * gr;
           float yl = 2.f * ca * gl2 * gl, yr = 2.f * ca * gr2 * gr;
@@ -492,9 +514,11 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
           }
           rhs += yr - yl;
           const bool real = i < n_u;
-          SB[r] = (real && i > 0) ? tho - s1 - ca * gl2 : 0.f;
-          IV[r] = real ? th + s0 + 2.f * s1 + ca * (gl2 + gr2) : 1.f;
-          CPr[r] = i < n_u - 1 ? tho - s1 - ca * gr2 : 0.f;
+          SB[r] = (real && i > 0) ? og - ca * gl2 : 0.f;
+          IV[r] = real ? dg + ca * (gl2 + gr2) : 1.f;
+          CPr[r] = i < n_u - 1 ? og - ca * gr2 : 0.f;
+          DG0[r] = IV[r];
+          CP0[r] = CPr[r];
         }
         RA[r] = i < n_u ? rhs : 0.f;
       }
@@ -511,6 +535,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         } else {
           tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
         }
+        if (refine) refine_solve(RA, AC);
       } else {
         // ---- stage 2: longitudinal right-hand side ----
         float dzmax = 0.f;   // lane's largest |Dz|: scale of the longitudinal increments
@@ -544,6 +569,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
 #pragma unroll
           for (int r = 0; r < MU; ++r)
             AC[r] = RA[r] + cb * (GR[r] * (AZe[r + 2] - AZe[r + 1]) - GL[r] * (AZe[r + 1] - AZe[r]));
+          float BC[MU];
+#pragma unroll
+          for (int r = 0; r < MU; ++r) BC[r] = AC[r];
           if (need_resp) {
             float xz[MU], XZe[MU + 2];
 #pragma unroll
@@ -557,6 +585,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
           } else {
             tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
           }
+          if (refine) refine_solve(BC, AC);
           // nodal d_+[g d(.)] of the new accelerations for the longitudinal rows
           {
             float ACe[MU + 2], fc[MU];

@@ -29,8 +29,8 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   const bool zjac = Dp->z_jacobi != 0;
   const int exc = Dp->exc;
   const int RU = kWarp * m_u + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
-  const float th = Dp->th, tho = Dp->tho, s0 = Dp->s0, s1 = Dp->s1, s1l = Dp->s1l;
-  const float lam2_0 = Dp->lam2, mu2 = Dp->mu2, lam2l_0 = Dp->lam2l;
+  const float dg = Dp->dg, og = Dp->og, s0 = Dp->s0, s0u = Dp->s0u, s1 = Dp->s1, s1l = Dp->s1l;
+  const float lam2_0 = Dp->lam2, mu2 = Dp->mu2, lam2l_0 = Dp->lam2l, lam2lo_0 = Dp->lam2_lo;
   const float ca_0 = Dp->ca, cb_0 = Dp->cb, cz_0 = Dp->cz;
   const float bsgn = Dp->boundary == 1 ? -1.f : 1.f;
   const int mod_kind = Dp->mod_kind;
@@ -132,9 +132,9 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   for (int r = 0; r < m_u; ++r) {
     const int i = ub + r;
     if (i < n_u) {
-      SUB[i] = i > 0 ? tho - s1 : 0.f;
-      INV[i] = th + s0 + 2.f * s1;
-      CP[i] = i < n_u - 1 ? tho - s1 : 0.f;
+      SUB[i] = i > 0 ? og : 0.f;
+      INV[i] = dg;
+      CP[i] = i < n_u - 1 ? og : 0.f;
     } else {
       SUB[i] = 0.f; INV[i] = 1.f; CP[i] = 0.f;
     }
@@ -208,6 +208,8 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         rm = exp2f(static_cast<float>(Dp->mod_inc * static_cast<double>(n)));
       }
       const float lam2 = lam2_0 * rm, lam2l = lam2l_0 * rm;
+      // low part of lam2_0 * rm (exact product residual plus the stored low part)
+      const float lam2_lo = fmaf(lam2_0, rm, -lam2) + lam2lo_0 * rm;
       const float ca = ca_0 * rm, cb = cb_0 * rm, cz = cz_0 * rm;
 
       // excitation scalars at time level n
@@ -245,7 +247,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         if (i == n_u - 1) d4 += bsgn * u0;
         const float du0 = DU[i];
         const float d2du = (DU[i + 1] - du0) - (du0 - DU[i - 1]);
-        float rhs = lam2 * d2 - mu2 * d4 - 2.f * s0 * du0 + 2.f * s1 * d2du;
+        float rhs = fmaf(lam2, d2, lam2_lo * d2) - mu2 * d4 - 2.f * s0u * du0 + 2.f * s1 * d2du;
         if (!linear) {
           const float gl2 = gl * gl, gr2 = gr * gr;
           float yl = 2.f * ca * gl2 * gl, yr = 2.f * ca * gr2 * gr;
@@ -255,9 +257,9 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
             FV[i] = gr2 - gl2;
           }
           rhs += yr - yl;
-          SUB[i] = i > 0 ? tho - s1 - ca * gl2 : 0.f;
-          INV[i] = th + s0 + 2.f * s1 + ca * (gl2 + gr2);
-          CP[i] = i < n_u - 1 ? tho - s1 - ca * gr2 : 0.f;
+          SUB[i] = i > 0 ? og - ca * gl2 : 0.f;
+          INV[i] = dg + ca * (gl2 + gr2);
+          CP[i] = i < n_u - 1 ? og - ca * gr2 : 0.f;
           G[i] = gl;
           if (i == n_u - 1) G[i + 1] = gr;
         }

@@ -38,10 +38,13 @@ struct Desc {
   int32_t linear;         // alpha == 1: z stays zero, matrix constant
   int32_t mod_kind;       // 0 none, 1 vibrato, 2 glissando
   int32_t z_jacobi;       // longitudinal off-diagonal folded into the sweeps
-  int32_t pad0_;
-  // delta-form coefficients (k^2-scaled Eq. 4), see the kernel
-  float th, tho;          // theta, (1 - theta)/2
-  float s0, s1, s1l;      // sigma0 k, sigma1 k / h_t^2, sigma1 k / h_l^2
+  int32_t refine;         // one step of iterative refinement per transverse solve
+  // delta-form coefficients (k^2-scaled Eq. 4), see the kernel.  The
+  // transverse equation (dg, og, s0u, s1, lam2, mu2, ca, cb, jscale) is
+  // multiplied by a scale beta that makes dg and og exact floats.
+  float dg, og;           // beta (theta + s0 + 2 s1), beta ((1 - theta)/2 - s1)
+  float s0, s1, s1l;      // sigma0 k (longitudinal), beta sigma1 k / h_t^2, sigma1 k / h_l^2
+  float s0u;              // beta sigma0 k (transverse)
   float lam2, mu2, lam2l; // g^2 k^2 / h_t^2, kappa^2 k^2 / h_t^4, g^2 alpha^2 k^2 / h_l^2
   float ca, cb, cz;       // phi' k^2 / (2 h_t^4), phi' k^2 / (2 h_t^3), phi' k^2 / (2 h_t^2 h_l)
   float out_scale;        // L (output in metres)
@@ -66,7 +69,7 @@ struct Desc {
   double mod_inc;         // vibrato: rate k (cycles per step); gliss: 2 D k / T
   double mod_phase0;      // vibrato: phase / (2 pi)
   float mod_depth2;       // vibrato: 2 c / 1200
-  float pad_;
+  float lam2_lo;          // lam2 + lam2_lo: wave coefficient to ~1e-15 (see fill_desc)
   // state (device pointers into the string's pool block)
   float* u;               // u^n            [n_u]
   float* du;              // u^n - u^{n-1}  [n_u]

@@ -87,6 +87,10 @@ def lib() -> ctypes.CDLL:
         "sfd_batch_synthesize": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
         "sfd_batch_synthesize_host": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
         "sfd_batch_destroy": (i32, [vp]),
+        "sfd_batch_set_warps_per_cta": (i32, [vp, i32]),
+        "sfd_batch_autotune": (i32, [vp, i64, P(i32)]),
+        "sfd_batch_prepare": (i32, [vp, P(i64), vp, P(i64)]),
+        "sfd_batch_launch": (i32, [vp]),
         "sfd_last_launch_count": (i32, [vp]),
         "sfd_ctx_transfer_bytes": (i32, [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "sfd_ctx_set_timing": (i32, [vp, i32]),
@@ -247,6 +251,27 @@ def sfd_batch_synthesize_host(b: int, n_samples, out_offsets=None, allow_noconv:
     if bad:
         raise SfdError(bad[0], f"{len(bad)} string(s) reported {STATUS_NAMES.get(bad[0])}")
     return [out[o:o + n] for o, n in zip(offs, ns)], st
+
+
+def sfd_batch_set_warps_per_cta(b: int, wpc: int) -> None:
+    _check(lib().sfd_batch_set_warps_per_cta(b, wpc))
+
+
+def sfd_batch_autotune(b: int, probe_samples: int) -> int:
+    best = ctypes.c_int32()
+    _check(lib().sfd_batch_autotune(b, probe_samples, ctypes.byref(best)))
+    return best.value
+
+
+def sfd_batch_prepare(b: int, n_samples, out_device, out_offsets) -> None:
+    ns = np.ascontiguousarray(n_samples, dtype=np.int64)
+    offs = np.ascontiguousarray(out_offsets, dtype=np.int64)
+    ptr = out_device if isinstance(out_device, int) else out_device.data_ptr()
+    _check(lib().sfd_batch_prepare(b, _i64p(ns), ptr, _i64p(offs)))
+
+
+def sfd_batch_launch(b: int) -> None:
+    _check(lib().sfd_batch_launch(b))
 
 
 def sfd_batch_destroy(b: int) -> None:

@@ -1,0 +1,188 @@
+"""Batching of uneven strings with f0 modulation (4096 strings of uneven N in
+one launch per kernel class, CUDA-graph replay, autotuned warps per CTA):
+results must not depend on how a batch is launched, and a subset of the
+modulated workload must match the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_18505_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sfd():
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd as S
+    return S
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_batch(sfd, ctx, strings):
+    hs = [sfd.string_from_dict(ctx, d) for d in strings]
+    return hs, sfd.sfd_batch_create(ctx, hs)
+
+
+def free(sfd, hs, b):
+    sfd.sfd_batch_destroy(b)
+    for h in hs:
+        sfd.sfd_string_destroy(h)
+
+
+def test_graph_replay_equals_direct_chunks(sfd):
+    """Chunks of 1024 samples: a captured CUDA graph replayed 6 times gives
+    bitwise the samples of 6 direct batch calls."""
+    stream = torch.cuda.Stream()
+    ctx = sfd.sfd_ctx_create(0, stream.cuda_stream, 256 << 20)
+    try:
+        strings = W.batch_modulated(48, seconds=0.2, seed=31)
+        n, chunks = 1024, 6
+        ns = np.full(len(strings), n, np.int64)
+        offs = np.arange(len(strings), dtype=np.int64) * n
+        # direct
+        hs, b = make_batch(sfd, ctx, strings)
+        out = torch.zeros(len(strings) * n, device="cuda")
+        direct = []
+        with torch.cuda.stream(stream):
+            for _ in range(chunks):
+                sfd.sfd_batch_synthesize(b, ns, out, offs)
+                direct.append(out.cpu().numpy().copy())
+        free(sfd, hs, b)
+        # captured
+        hs, b = make_batch(sfd, ctx, strings)
+        out2 = torch.zeros(len(strings) * n, device="cuda")
+        sfd.sfd_batch_prepare(b, ns, out2, offs)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sfd.sfd_batch_launch(b)
+        graphed = []
+        for _ in range(chunks):
+            g.replay()
+            torch.cuda.synchronize()
+            graphed.append(out2.cpu().numpy().copy())
+        # the capture itself did not run the kernels: state advanced only by replays
+        free(sfd, hs, b)
+        for a, c in zip(direct, graphed):
+            assert np.array_equal(a, c)
+    finally:
+        torch.cuda.synchronize()
+        sfd.sfd_ctx_destroy(ctx)
+
+
+def test_autotune_does_not_advance_strings(sfd):
+    ctx = sfd.sfd_ctx_create(0, None, 256 << 20)
+    try:
+        strings = W.batch_mixed(40, seconds=0.05, seed=41)
+        ns = [d["n_samples"] for d in strings]
+        hs, b = make_batch(sfd, ctx, strings)
+        best = sfd.sfd_batch_autotune(b, 256)
+        assert best in (1, 2, 4)
+        ys, _ = sfd.sfd_batch_synthesize_host(b, ns)
+        free(sfd, hs, b)
+        hs, b = make_batch(sfd, ctx, strings)
+        ref, _ = sfd.sfd_batch_synthesize_host(b, ns)
+        free(sfd, hs, b)
+        for a, c in zip(ys, ref):
+            assert np.array_equal(a, c)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("wpc", [1, 2, 4])
+def test_warps_per_cta_does_not_change_results(sfd, wpc):
+    ctx = sfd.sfd_ctx_create(0, None, 256 << 20)
+    try:
+        strings = W.batch_mixed(20, seconds=0.03, seed=43)
+        ns = [d["n_samples"] for d in strings]
+        hs, b = make_batch(sfd, ctx, strings)
+        sfd.sfd_batch_set_warps_per_cta(b, wpc)
+        ys, _ = sfd.sfd_batch_synthesize_host(b, ns)
+        free(sfd, hs, b)
+        for d, y in zip(strings, ys):
+            s = sfd.string_from_dict(ctx, d)
+            assert np.array_equal(y, sfd.sfd_synthesize(s, d["n_samples"]))
+            sfd.sfd_string_destroy(s)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
+
+
+def test_modulated_uneven_subset_matches_oracle(sfd):
+    """Strings of the 4096-string modulated workload (f0 30-2000 Hz, vibrato
+    and glissando, uneven N) synthesized together in one batch: the first
+    0.25 s of a spread of them against the oracle (bowed: 150 samples)."""
+    ctx = sfd.sfd_ctx_create(0, None, 512 << 20)
+    try:
+        full = W.batch_modulated(4096, seconds=4.0, seed=3)
+        picks = [0, 1, 2, 3, 100, 101, 777, 1500, 2048, 3001, 4094, 4095]
+        strings = [dict(full[i], n_samples=12000) for i in picks]
+        grids = [oracle.grid(d) for d in strings]
+        assert min(g[0] for g in grids) < 20 and max(g[0] for g in grids) > 60   # uneven N
+        hs, b = make_batch(sfd, ctx, strings)
+        ys, st = sfd.sfd_batch_synthesize_host(b, [12000] * len(strings))
+        free(sfd, hs, b)
+        assert np.all(st == 0)
+        for d, y in zip(strings, ys):
+            n = 150 if d["excitation"]["kind"] == "bow" else 12000
+            ref = oracle.run(d, n)
+            assert rel_l2(y[:n], ref) <= (1e-3 if n == 150 else TOL), (d["f0"], d["modulation"])
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
+
+
+def test_highest_f0_modulated_strings_match_oracle(sfd):
+    """The 24 highest non-bowed notes of the modulated workload (f0 about
+    1.9-2 kHz, grids of 3-8 intervals): the most periods in 0.25 s, so the
+    largest phase error FP32 coefficients or factors could accumulate."""
+    ctx = sfd.sfd_ctx_create(0, None, 256 << 20)
+    try:
+        full = W.batch_modulated(4096, seconds=4.0, seed=3)
+        order = sorted((i for i in range(len(full)) if full[i]["excitation"]["kind"] != "bow"),
+                       key=lambda i: -full[i]["f0"])[:24]
+        strings = [dict(full[i], n_samples=12000) for i in order]
+        assert min(d["f0"] for d in strings) > 1800
+        hs, b = make_batch(sfd, ctx, strings)
+        ys, st = sfd.sfd_batch_synthesize_host(b, [12000] * len(strings))
+        free(sfd, hs, b)
+        assert np.all(st == 0)
+        refs, _ = oracle.run_batch(strings, n_samples=12000)
+        for d, y, ref in zip(strings, ys, refs):
+            assert rel_l2(y, ref) <= TOL, (d["f0"], d["modulation"])
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
+
+
+def test_modulated_batch_all_finite(sfd):
+    """512 strings of the modulated workload, 0.5 s, graph-replayed in 4
+    chunks: every sample finite and every string's status OK."""
+    stream = torch.cuda.Stream()
+    ctx = sfd.sfd_ctx_create(0, stream.cuda_stream, 512 << 20)
+    try:
+        strings = W.batch_modulated(512, seconds=0.5, seed=3)
+        n = 6000
+        ns = np.full(len(strings), n, np.int64)
+        offs = np.arange(len(strings), dtype=np.int64) * n
+        hs, b = make_batch(sfd, ctx, strings)
+        out = torch.zeros(len(strings) * n, device="cuda")
+        sfd.sfd_batch_prepare(b, ns, out, offs)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sfd.sfd_batch_launch(b)
+        for _ in range(4):
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.isfinite(out).all().item()
+        for h in hs:
+            assert sfd.sfd_string_stats(h)[0] == 0
+        free(sfd, hs, b)
+    finally:
+        torch.cuda.synchronize()
+        sfd.sfd_ctx_destroy(ctx)
