@@ -217,6 +217,10 @@ WORKLOAD_MODULATED = ("4096 strings x 4 s at 48 kHz, uneven N: f0 log-U[30,2000]
 
 
 def make_workload(args, rank):
+    if args.workload == "serving":
+        trace = W.serving_trace(args.rate, args.trace_seconds, seed=5 + 1000 * rank)
+        return [d for _, d in trace], WORKLOAD_SERVING.format(rate=args.rate, secs=args.trace_seconds,
+                                                              live=args.max_live)
     if args.workload == "modulated":
         return W.batch_modulated(args.strings or 4096, seconds=args.seconds or 4.0, seed=3 + 1000 * rank), \
             WORKLOAD_MODULATED
@@ -444,27 +448,126 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ serving
+
+WORKLOAD_SERVING = ("serving: Poisson note requests at {rate:g}/s for {secs:g} s (seed 5), f0 log-U[40,1000] Hz, "
+                    "duration U[0.25,4] s, params and excitations as the mixed batch, 1024-sample chunks, "
+                    "admission by device memory, up to {live} live notes")
+
+
+def run_serving(args, ws, rank, local):
+    """Replay the arrival trace in real time through the serving API: submit
+    each request at its arrival time, pump (admit, launch the next chunk,
+    deliver the previous one) until every note has been delivered.  Reports
+    delivered samples/s, first-chunk latency percentiles and the real-time
+    factor (audio seconds delivered per wall second)."""
+    import torch
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    secs = args.trace_seconds
+    trace = W.serving_trace(args.rate, secs, seed=5 + 1000 * rank)
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 2 << 30)
+    sv = sfd.sfd_server_create(ctx, 1024, args.max_live)
+    reqs = [sfd.request_from_dict(d, i) for i, (_, d) in enumerate(trace)]   # marshalled before the clock starts
+
+    def drained():
+        st = sfd.sfd_server_stats_get(sv)
+        return st.queued == 0 and st.live == 0 and st.in_flight == 0
+
+    # warm-up: a burst of short notes through the same path
+    for i, (_, d) in enumerate(W.serving_trace(args.rate, 0.05, seed=99)):
+        sfd.sfd_server_submit(sv, sfd.request_from_dict(d, 10 ** 9 + i, n_samples=3000))
+    while not drained():
+        sfd.sfd_server_pump(sv, copy=False)
+
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = sfd.sfd_server_clock(sv) + 0.01
+    n, i = len(trace), 0
+    lat, samples, notes_done, peak_queue, peak_live, pumps = [], 0, 0, 0, 0, 0
+    while True:
+        now = sfd.sfd_server_clock(sv)
+        while i < n and t0 + trace[i][0] <= now:
+            reqs[i].arrival_s = t0 + trace[i][0]
+            sfd.sfd_server_submit(sv, reqs[i])
+            i += 1
+        st = sfd.sfd_server_stats_get(sv)
+        peak_queue, peak_live = max(peak_queue, st.queued), max(peak_live, st.live)
+        if st.queued == 0 and st.live == 0 and st.in_flight == 0:
+            if i == n:
+                break
+            time.sleep(max(0.0, min(0.002, t0 + trace[i][0] - now)))
+            continue
+        for tag, first, cnt, last, status, ready, arrival in sfd.sfd_server_pump(sv, copy=False):
+            if first == 0:
+                lat.append(ready - arrival)
+            samples += cnt
+            notes_done += last
+        pumps += 1
+    t1 = sfd.sfd_server_clock(sv)
+    clk = clocks.stop()
+    h0, d0 = sfd.sfd_ctx_transfer_bytes(ctx)
+    sfd.sfd_server_destroy(sv)
+    sfd.sfd_ctx_destroy(ctx)
+    wall = max_over_ranks(ws, t1 - t0)
+    if rank != 0:
+        return 0
+    lat_ms = np.array(lat) * 1e3
+    audio_s = samples / FS
+    line = {
+        "metric": METRIC, "value": ws * samples / wall, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 1,
+        "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SERVING.format(rate=args.rate, secs=secs, live=args.max_live),
+                   "notes": n, "offered_audio_s": float(sum(d["n_samples"] for _, d in trace) / FS),
+                   "l2": "not flushed (serving replay: state stays resident by design)"},
+        "serving": {"first_chunk_latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                               "p99": float(np.percentile(lat_ms, 99)),
+                                               "max": float(lat_ms.max())},
+                    "realtime_factor": ws * audio_s / wall, "notes_completed": notes_done,
+                    "peak_live": peak_live, "peak_queued": peak_queue, "pumps": pumps,
+                    "wall_s": wall, "trace_s": secs},
+        "e2e": {"value": ws * samples / wall, "unit": UNIT, "h2d_bytes_per_step": int(h0), "d2h_bytes_per_step": int(d0)},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: note requests per second")
+    ap.add_argument("--trace-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
+    ap.add_argument("--max-live", type=int, default=8192, help="serving: live-note slots")
     ap.add_argument("--strings", type=int, default=0)
     ap.add_argument("--seconds", type=float, default=0.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-strings", type=int, default=64)
-    ap.add_argument("--cpu-samples", type=int, default=36000)
-    ap.add_argument("--ref-strings", type=int, default=64)
-    ap.add_argument("--ref-samples", type=int, default=36000)
+    # oracle samples: the whole 256 x 2 s batch for the baseline (~17 s on 16
+    # cores), half of it per step for the reference arm
+    ap.add_argument("--cpu-strings", type=int, default=256)
+    ap.add_argument("--cpu-samples", type=int, default=96000)
+    ap.add_argument("--ref-strings", type=int, default=128)
+    ap.add_argument("--ref-samples", type=int, default=96000)
     args = ap.parse_args(argv)
     ws, rank, local = dist_setup(args.gpus)
     try:
         if args.impl == "reference":
             return run_reference(args, ws, rank)
+        if args.workload == "serving":
+            return run_serving(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1:

@@ -220,8 +220,8 @@ sfd_status sfd_batch_launch(sfd_batch* b);
 
 sfd_status sfd_batch_destroy(sfd_batch* b);
 
-/* Excitation of a string for sfd_synthesize_noalloc (same meaning and units
- * as the sfd_excite_* calls).  kind: 0 pluck (amp_m, pos), 1 hammer
+/* Excitation of a string for sfd_synthesize_noalloc and sfd_server_submit
+ * (same meaning and units as the sfd_excite_* calls).  kind: 0 pluck (amp_m, pos), 1 hammer
  * (mass_kg, vel_mps, pos, omega_h, alpha_h), 2 bow (vel_mps, force_n, pos,
  * a_s_per_m, eps, release_time_s). */
 typedef struct {
@@ -255,6 +255,78 @@ typedef struct {
  * the string's status).  f0 modulation is not available here. */
 sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, const sfd_string_params* params,
                                   const sfd_excitation* exc, int64_t n_samples, float* out_device);
+
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of note requests.  There is no counterpart
+ * in the paper (its synthesizer renders one batch offline); the notes are
+ * the same strings, stepped by the same kernels.
+ *
+ * A server owns a context's stream.  Requests (a note: string parameters,
+ * excitation, optional f0 modulation, length in samples) are queued by
+ * sfd_server_submit on the host.  Each sfd_server_pump
+ *   1. admits queued requests in arrival order while the server has a free
+ *      slot and the context's device pool a block for the note's state
+ *      (admission by device memory; a request that does not fit waits,
+ *      later ones wait behind it);
+ *   2. enqueues the next chunk (chunk_samples, fewer at a note's end) of
+ *      every live note as one persistent launch per kernel class, and the
+ *      copy of the chunk's audio to pinned host memory;
+ *   3. waits for the chunk enqueued by the previous pump and returns its
+ *      audio, one sfd_chunk per live note (so a pump's host work overlaps
+ *      the next chunk's GPU work);
+ *   4. frees the slots and blocks of the notes that ended in that chunk.
+ * A note's audio is bitwise the audio of the same string synthesized alone
+ * (chunking and batching do not change a string's arithmetic).  Not
+ * thread-safe; one server per context.
+ * --------------------------------------------------------------------- */
+typedef struct sfd_server sfd_server;
+
+typedef struct {
+  sfd_string_params params;
+  sfd_excitation exc;
+  int32_t mod_kind;         /* SFD_MOD_NONE / VIBRATO / GLISS (sfd_set_modulation) */
+  int32_t pad_;
+  double mod_rate_hz, mod_depth, mod_phase_rad, mod_duration_s;
+  int64_t n_samples;        /* note length (> 0) */
+  double arrival_s;         /* arrival on the server clock; < 0: the submit time */
+  uint64_t tag;             /* caller's id, returned with every chunk */
+} sfd_request;
+
+typedef struct {
+  uint64_t tag;
+  int64_t first_sample;     /* index of the chunk's first sample within the note */
+  int32_t n;                /* samples in this chunk */
+  int32_t last;             /* 1 on the note's final chunk */
+  sfd_status status;        /* on the final chunk: SFD_OK, SFD_EUNSTABLE or SFD_ENOCONV */
+  int32_t pad_;
+  const float* samples;     /* n samples (metres), pinned host memory owned by the
+                               server, valid until the next sfd_server_pump */
+  double ready_s;           /* server clock when the chunk's audio was on the host */
+  double arrival_s;         /* the request's arrival */
+} sfd_chunk;
+
+typedef struct {
+  int64_t queued, live, submitted, admitted, completed, chunks, samples;
+  int64_t in_flight;        /* 1 while a chunk is enqueued and not yet returned */
+  uint64_t pool_used, pool_size;
+} sfd_server_stats;
+
+/* chunk_samples > 0, max_live > 0 slots.  The server's output and job
+ * buffers (2 x max_live x chunk_samples floats on the device, the same in
+ * pinned host memory) are taken from the context's pool and the host;
+ * SFD_ENOMEM if they do not fit. */
+sfd_status sfd_server_create(sfd_ctx* ctx, int32_t chunk_samples, int32_t max_live, sfd_server** out);
+/* Validates and queues a request (host only).  SFD_EINVAL for invalid
+ * parameters, SFD_ENOMEM for a note whose state can never fit the pool. */
+sfd_status sfd_server_submit(sfd_server* sv, const sfd_request* req);
+/* One admission + launch + delivery round (see above).  *chunks points to
+ * *n_chunks records owned by the server, valid until the next pump. */
+sfd_status sfd_server_pump(sfd_server* sv, const sfd_chunk** chunks, int32_t* n_chunks);
+/* Seconds since the server was created (steady clock). */
+double sfd_server_clock(const sfd_server* sv);
+sfd_status sfd_server_stats_get(const sfd_server* sv, sfd_server_stats* st);
+/* Waits for any chunk in flight, frees every note and the buffers. */
+sfd_status sfd_server_destroy(sfd_server* sv);
 
 /* Thread-local message describing the last error. */
 const char* sfd_last_error(void);

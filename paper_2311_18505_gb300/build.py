@@ -1,6 +1,7 @@
 """Build the CUDA library libsfd.so for sm_103a (in-tree, no cmake).
 
-Two translation units are compiled in parallel with nvcc and linked into
+The host runtime and the per-class step kernels are compiled in parallel
+with nvcc and linked into
 ``paper_2311_18505_gb300/_build/libsfd.so``.
 """
 
@@ -24,7 +25,7 @@ UNITS = [("sfd_api.cu", "sfd_api.o", [])] + \
         [("sfd_kernel.cu", f"sfd_kernel_r{mu}.o", [f"-DSFD_MU={mu}"]) for mu in (1, 3, 5, 7, 9)] + \
         [("sfd_kernel.cu", "sfd_kernel_smem.o", [])]
 SOURCES = sorted({u[0] for u in UNITS})
-HEADERS = ["sfd_types.h", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh"]
+HEADERS = ["sfd_types.h", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_server.cuh"]
 
 
 def nvcc() -> str:

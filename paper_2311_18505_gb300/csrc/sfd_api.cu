@@ -369,37 +369,158 @@ void carve(sfd_string* s) {
   D.sc = s->d_sc;
 }
 
-// Upload the descriptor and the initial state (w^0, w^1 of Sec. 3.4).
-sfd_status upload_initial(sfd_string* s) {
+// Host image of a carved string's whole pool block (block_bytes(s->h)
+// bytes at img): the descriptor, the scalars and the initial state w^0, w^1
+// of Sec. 3.4 (pluck triangle or rest; the hammer at the rest position
+// moving with v_H), zero elsewhere.
+void write_image(const sfd_string* s, char* img) {
   const Desc& D = s->h;
-  std::vector<float> u(D.n_u, 0.f), du(D.n_u, 0.f);
-  const size_t nz = D.n_z > 0 ? D.n_z : 1;
-  std::vector<float> zero(nz, 0.f);
+  const size_t bytes = block_bytes(D);
+  std::memset(img, 0, bytes);
+  auto at = [&](const void* dev) { return img + (static_cast<const char*>(dev) - s->block); };
+  std::memcpy(at(s->d_desc), &D, sizeof(Desc));
   Scalars sc{};
   sc.n = 1;
   sc.next_out = 0;
+  if (s->exc == kHammer) {
+    sc.uh = static_cast<float>(s->hammer_uh1);
+    sc.duh = static_cast<float>(s->hammer_uh1);
+  }
+  std::memcpy(at(s->d_sc), &sc, sizeof(Scalars));
   if (s->exc == kPluck && s->pluck_amp != 0.0) {
+    float* u = reinterpret_cast<float*>(at(D.u));
     const double c0 = s->pluck_amp / s->p.length_m, xp = s->pluck_pos;
     for (int l = 1; l < s->n_t; ++l) {
       const double x = static_cast<double>(l) / s->n_t;
       u[l - 1] = static_cast<float>(x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp));
     }
   }
-  if (s->exc == kHammer) {
-    // the hammer starts at the string's rest position moving with v_H
-    sc.uh = static_cast<float>(s->hammer_uh1);
-    sc.duh = static_cast<float>(s->hammer_uh1);
-  }
+}
+
+// Upload the descriptor and the initial state (one copy of the block image).
+sfd_status upload_initial(sfd_string* s) {
+  std::vector<char> img(block_bytes(s->h));
+  write_image(s, img.data());
   sfd_ctx* c = s->ctx;
-  SFD_CUDA(h2d(c, s->d_desc, &s->h, sizeof(Desc)));
-  SFD_CUDA(h2d(c, s->d_sc, &sc, sizeof(Scalars)));
-  SFD_CUDA(h2d(c, D.u, u.data(), sizeof(float) * D.n_u));
-  SFD_CUDA(h2d(c, D.du, du.data(), sizeof(float) * D.n_u));
-  SFD_CUDA(h2d(c, D.z, zero.data(), sizeof(float) * nz));
-  SFD_CUDA(h2d(c, D.dz, zero.data(), sizeof(float) * nz));
-  SFD_CUDA(h2d(c, D.xz, zero.data(), sizeof(float) * nz));
-  SFD_CUDA(h2d(c, D.az, zero.data(), sizeof(float) * nz));
+  SFD_CUDA(h2d(c, s->block, img.data(), img.size()));
   SFD_CUDA(cudaStreamSynchronize(c->stream));
+  return SFD_OK;
+}
+
+// Defaults and validation of string parameters (SI units, Table 1 ranges
+// are not enforced, only what the scheme needs); gamma = 2 f0 unless given.
+sfd_status normalize_params(sfd_string_params& q, double* gamma_out) {
+  if (q.length_m == 0) q.length_m = 1.0;
+  if (q.fs == 0) q.fs = 48000.0;
+  if (q.linear_density == 0) q.linear_density = 5e-3;
+  if (q.theta == 0) q.theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
+  if (q.pickup_pos == 0) q.pickup_pos = 0.7;
+  if (q.f0_max_ratio < 1.0) q.f0_max_ratio = 1.0;
+  const double gamma = q.gamma > 0 ? q.gamma : 2.0 * q.f0;
+  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(SFD_EINVAL, "f0/gamma must be > 0");
+  if (!(q.fs > 0)) return fail(SFD_EINVAL, "fs must be > 0");
+  if (!(q.kappa >= 0)) return fail(SFD_EINVAL, "kappa must be >= 0");
+  if (!(q.alpha >= 1.0)) return fail(SFD_EINVAL, "alpha must be >= 1");
+  if (!(q.sigma0 >= 0) || !(q.sigma1 >= 0)) return fail(SFD_EINVAL, "losses must be >= 0");
+  if (!(q.theta > 0.5 && q.theta <= 1.0)) return fail(SFD_EINVAL, "theta must be in (1/2, 1]");
+  if (!(q.pickup_pos > 0 && q.pickup_pos < 1)) return fail(SFD_EINVAL, "pickup must be in (0, 1)");
+  if (!(q.length_m > 0) || !(q.linear_density > 0)) return fail(SFD_EINVAL, "length and density must be > 0");
+  if (q.boundary != 0 && q.boundary != 1) return fail(SFD_EINVAL, "bad boundary");
+  if (q.grid_rule != 0 && q.grid_rule != 1) return fail(SFD_EINVAL, "bad grid rule");
+  *gamma_out = gamma;
+  return SFD_OK;
+}
+
+// Host part of sfd_string_create: parameters, grid and descriptor (no
+// device access; s->ctx, block and device pointers are left unset).
+sfd_status init_host_string(const sfd_string_params& p, sfd_string* s) {
+  s->p = p;
+  double gamma = 0;
+  sfd_status rc = normalize_params(s->p, &gamma);
+  if (rc) return rc;
+  int n_t = 0, n_l = 0;
+  if ((rc = derive_grid(s->p, gamma * s->p.f0_max_ratio, &n_t, &n_l))) return rc;
+  s->gamma = gamma;
+  s->k = 1.0 / s->p.fs;
+  s->n_t = n_t;
+  s->n_l = n_l;
+  s->exc = kPluck;
+  s->h.bow_release_n = INT64_MAX;
+  fill_desc(s);
+  return SFD_OK;
+}
+
+// Excitation of Sec. 3.3 / Eqs. 5-6 set on the host copy (as the
+// sfd_excite_* calls do; the pluck is the initial condition).
+sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
+  const sfd_string_params& q = s->p;
+  const double pos = ex.pos;
+  if (!(pos > 0 && pos < 1)) return fail(SFD_EINVAL, "excitation position must be in (0, 1)");
+  if (ex.kind == kPluck) {
+    if (!std::isfinite(ex.amp_m)) return fail(SFD_EINVAL, "bad pluck amplitude");
+    s->exc = kPluck;
+    s->pluck_amp = ex.amp_m;
+    s->pluck_pos = pos;
+    fill_desc(s);
+  } else if (ex.kind == kHammer) {
+    if (!(ex.mass_kg > 0) || !(ex.omega_h > 0) || !(ex.alpha_h >= 1) || !std::isfinite(ex.vel_mps))
+      return fail(SFD_EINVAL, "bad hammer parameters");
+    s->exc = kHammer;
+    s->pluck_amp = 0;
+    fill_desc(s);
+    point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+    s->h.ham_M = static_cast<float>(ex.mass_kg / (q.linear_density * q.length_m));
+    s->h.ham_k2w = static_cast<float>(s->k * s->k * std::pow(ex.omega_h, 1.0 + ex.alpha_h));
+    s->h.ham_expo = static_cast<float>(ex.alpha_h - 1.0);
+    s->hammer_uh1 = (ex.vel_mps / q.length_m) * s->k;
+  } else if (ex.kind == kBow) {
+    if (!(ex.force_n >= 0) || !(ex.eps >= 0 && ex.eps <= 1) || !(ex.a_s_per_m >= 0) || !std::isfinite(ex.vel_mps))
+      return fail(SFD_EINVAL, "bad bow parameters");
+    s->exc = kBow;
+    s->pluck_amp = 0;
+    fill_desc(s);
+    point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+    s->h.bow_F = static_cast<float>(ex.force_n / (q.linear_density * q.length_m * q.length_m));
+    s->h.bow_v = static_cast<float>(ex.vel_mps / q.length_m);
+    s->h.bow_a = static_cast<float>(ex.a_s_per_m * q.length_m);
+    s->h.bow_eps = static_cast<float>(ex.eps);
+    s->h.bow_release_n = INT64_MAX;
+    if (ex.release_time_s >= 0) {
+      // first step n with n k >= release
+      int64_t n = static_cast<int64_t>(std::ceil(ex.release_time_s * q.fs));
+      while (n > 0 && static_cast<double>(n - 1) * s->k >= ex.release_time_s) --n;
+      while (static_cast<double>(n) * s->k < ex.release_time_s) ++n;
+      s->h.bow_release_n = n;
+    }
+  } else {
+    return fail(SFD_EINVAL, "bad excitation kind %d", ex.kind);
+  }
+  return SFD_OK;
+}
+
+// f0 modulation on the host copy of the descriptor (reading A14).
+sfd_status apply_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth, double phase_rad,
+                            double duration_s) {
+  Desc& D = s->h;
+  if (kind == SFD_MOD_NONE) {
+    D.mod_kind = 0;
+  } else if (kind == SFD_MOD_VIBRATO) {
+    if (!std::isfinite(rate_hz) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad vibrato");
+    if (std::pow(2.0, std::fabs(depth) / 1200.0) > s->p.f0_max_ratio * (1.0 + 1e-12))
+      return fail(SFD_EINVAL, "vibrato peak exceeds the grid's f0_max_ratio");
+    D.mod_kind = 1;
+    D.mod_inc = rate_hz * s->k;
+    D.mod_phase0 = phase_rad / (2.0 * kPi);
+    D.mod_depth2 = static_cast<float>(2.0 * depth / 1200.0);
+  } else if (kind == SFD_MOD_GLISS) {
+    if (!(duration_s > 0) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad glissando");
+    if (std::pow(2.0, std::max(0.0, depth)) > s->p.f0_max_ratio * (1.0 + 1e-12))
+      return fail(SFD_EINVAL, "glissando peak exceeds the grid's f0_max_ratio");
+    D.mod_kind = 2;
+    D.mod_inc = 2.0 * depth * s->k / duration_s;
+  } else {
+    return fail(SFD_EINVAL, "bad modulation kind");
+  }
   return SFD_OK;
 }
 
@@ -677,38 +798,12 @@ sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* c, uint64_t* h2d_total, uint64_
 sfd_status sfd_string_create(sfd_ctx* c, const sfd_string_params* p, sfd_string** out) {
   if (!c || !p || !out) return fail(SFD_EINVAL, "NULL argument");
   *out = nullptr;
-  sfd_string_params q = *p;
-  if (q.length_m == 0) q.length_m = 1.0;
-  if (q.fs == 0) q.fs = 48000.0;
-  if (q.linear_density == 0) q.linear_density = 5e-3;
-  if (q.theta == 0) q.theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
-  if (q.pickup_pos == 0) q.pickup_pos = 0.7;
-  if (q.f0_max_ratio < 1.0) q.f0_max_ratio = 1.0;
-  const double gamma = q.gamma > 0 ? q.gamma : 2.0 * q.f0;
-  if (!(gamma > 0) || !std::isfinite(gamma)) return fail(SFD_EINVAL, "f0/gamma must be > 0");
-  if (!(q.fs > 0)) return fail(SFD_EINVAL, "fs must be > 0");
-  if (!(q.kappa >= 0)) return fail(SFD_EINVAL, "kappa must be >= 0");
-  if (!(q.alpha >= 1.0)) return fail(SFD_EINVAL, "alpha must be >= 1");
-  if (!(q.sigma0 >= 0) || !(q.sigma1 >= 0)) return fail(SFD_EINVAL, "losses must be >= 0");
-  if (!(q.theta > 0.5 && q.theta <= 1.0)) return fail(SFD_EINVAL, "theta must be in (1/2, 1]");
-  if (!(q.pickup_pos > 0 && q.pickup_pos < 1)) return fail(SFD_EINVAL, "pickup must be in (0, 1)");
-  if (!(q.length_m > 0) || !(q.linear_density > 0)) return fail(SFD_EINVAL, "length and density must be > 0");
-  if (q.boundary != 0 && q.boundary != 1) return fail(SFD_EINVAL, "bad boundary");
-  if (q.grid_rule != 0 && q.grid_rule != 1) return fail(SFD_EINVAL, "bad grid rule");
-  int n_t = 0, n_l = 0;
-  sfd_status rc = derive_grid(q, gamma * q.f0_max_ratio, &n_t, &n_l);
-  if (rc) return rc;
   sfd_string* s = new (std::nothrow) sfd_string();
   if (!s) return fail(SFD_ENOMEM, "host allocation failed");
+  sfd_status rc = init_host_string(*p, s);
+  if (rc) { delete s; return rc; }
   s->ctx = c;
-  s->p = q;
-  s->gamma = gamma;
-  s->k = 1.0 / q.fs;
-  s->n_t = n_t;
-  s->n_l = n_l;
-  s->exc = kPluck;
-  s->h.bow_release_n = INT64_MAX;
-  fill_desc(s);
+  const int n_t = s->n_t, n_l = s->n_l;
   const size_t wbytes = static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z, s->h.z_jacobi)) * sizeof(float);
   if (wbytes > c->smem_optin) {
     delete s;
@@ -806,27 +901,9 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
                               double duration_s) {
   if (!s) return fail(SFD_EINVAL, "string is NULL");
   if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
-  Desc& D = s->h;
-  if (kind == SFD_MOD_NONE) {
-    D.mod_kind = 0;
-  } else if (kind == SFD_MOD_VIBRATO) {
-    if (!std::isfinite(rate_hz) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad vibrato");
-    if (std::pow(2.0, std::fabs(depth) / 1200.0) > s->p.f0_max_ratio * (1.0 + 1e-12))
-      return fail(SFD_EINVAL, "vibrato peak exceeds the grid's f0_max_ratio");
-    D.mod_kind = 1;
-    D.mod_inc = rate_hz * s->k;
-    D.mod_phase0 = phase_rad / (2.0 * kPi);
-    D.mod_depth2 = static_cast<float>(2.0 * depth / 1200.0);
-  } else if (kind == SFD_MOD_GLISS) {
-    if (!(duration_s > 0) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad glissando");
-    if (std::pow(2.0, std::max(0.0, depth)) > s->p.f0_max_ratio * (1.0 + 1e-12))
-      return fail(SFD_EINVAL, "glissando peak exceeds the grid's f0_max_ratio");
-    D.mod_kind = 2;
-    D.mod_inc = 2.0 * depth * s->k / duration_s;
-  } else {
-    return fail(SFD_EINVAL, "bad modulation kind");
-  }
-  sfd_status rc = set_device(s->ctx);
+  sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
+  if (rc) return rc;
+  rc = set_device(s->ctx);
   if (rc) return rc;
   SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
   SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
@@ -1205,66 +1282,10 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
 
   // the string, as sfd_string_create + sfd_excite_* would set it up
   sfd_string s;
-  s.p = *params;
-  sfd_string_params& q = s.p;
-  if (q.length_m == 0) q.length_m = 1.0;
-  if (q.fs == 0) q.fs = 48000.0;
-  if (q.linear_density == 0) q.linear_density = 5e-3;
-  if (q.theta == 0) q.theta = 0.5 * (1.0 + 4.0 / (kPi * kPi));
-  if (q.pickup_pos == 0) q.pickup_pos = 0.7;
-  if (q.f0_max_ratio < 1.0) q.f0_max_ratio = 1.0;
-  const double gamma = q.gamma > 0 ? q.gamma : 2.0 * q.f0;
-  if (!(gamma > 0) || !std::isfinite(gamma) || !(q.fs > 0) || !(q.kappa >= 0) || !(q.alpha >= 1.0) ||
-      !(q.sigma0 >= 0) || !(q.sigma1 >= 0) || !(q.theta > 0.5 && q.theta <= 1.0) ||
-      !(q.pickup_pos > 0 && q.pickup_pos < 1) || !(q.length_m > 0) || !(q.linear_density > 0) ||
-      (q.boundary != 0 && q.boundary != 1) || (q.grid_rule != 0 && q.grid_rule != 1))
-    return fail(SFD_EINVAL, "invalid string parameters");
-  int n_t = 0, n_l = 0;
-  sfd_status rc = derive_grid(q, gamma * q.f0_max_ratio, &n_t, &n_l);
+  sfd_status rc = init_host_string(*params, &s);
   if (rc) return rc;
-  s.gamma = gamma;
-  s.k = 1.0 / q.fs;
-  s.n_t = n_t;
-  s.n_l = n_l;
-  s.h.bow_release_n = INT64_MAX;
-  const double pos = exc->pos;
-  if (!(pos > 0 && pos < 1)) return fail(SFD_EINVAL, "excitation position must be in (0, 1)");
-  if (exc->kind == kPluck) {
-    if (!std::isfinite(exc->amp_m)) return fail(SFD_EINVAL, "bad pluck amplitude");
-    s.exc = kPluck;
-    s.pluck_amp = exc->amp_m;
-    s.pluck_pos = pos;
-    fill_desc(&s);
-  } else if (exc->kind == kHammer) {
-    if (!(exc->mass_kg > 0) || !(exc->omega_h > 0) || !(exc->alpha_h >= 1) || !std::isfinite(exc->vel_mps))
-      return fail(SFD_EINVAL, "bad hammer parameters");
-    s.exc = kHammer;
-    fill_desc(&s);
-    point_weights(n_t, pos, &s.h.e_node, &s.h.e_w);
-    s.h.ham_M = static_cast<float>(exc->mass_kg / (q.linear_density * q.length_m));
-    s.h.ham_k2w = static_cast<float>(s.k * s.k * std::pow(exc->omega_h, 1.0 + exc->alpha_h));
-    s.h.ham_expo = static_cast<float>(exc->alpha_h - 1.0);
-    s.hammer_uh1 = (exc->vel_mps / q.length_m) * s.k;
-  } else if (exc->kind == kBow) {
-    if (!(exc->force_n >= 0) || !(exc->eps >= 0 && exc->eps <= 1) || !(exc->a_s_per_m >= 0) ||
-        !std::isfinite(exc->vel_mps))
-      return fail(SFD_EINVAL, "bad bow parameters");
-    s.exc = kBow;
-    fill_desc(&s);
-    point_weights(n_t, pos, &s.h.e_node, &s.h.e_w);
-    s.h.bow_F = static_cast<float>(exc->force_n / (q.linear_density * q.length_m * q.length_m));
-    s.h.bow_v = static_cast<float>(exc->vel_mps / q.length_m);
-    s.h.bow_a = static_cast<float>(exc->a_s_per_m * q.length_m);
-    s.h.bow_eps = static_cast<float>(exc->eps);
-    if (exc->release_time_s >= 0) {
-      int64_t n = static_cast<int64_t>(std::ceil(exc->release_time_s * q.fs));
-      while (n > 0 && static_cast<double>(n - 1) * s.k >= exc->release_time_s) --n;
-      while (static_cast<double>(n) * s.k < exc->release_time_s) ++n;
-      s.h.bow_release_n = n;
-    }
-  } else {
-    return fail(SFD_EINVAL, "bad excitation kind %d", exc->kind);
-  }
+  if ((rc = apply_excitation(&s, *exc))) return rc;
+  const int n_t = s.n_t, n_l = s.n_l;
   const Desc& D = s.h;
   const size_t wbytes = static_cast<size_t>(warp_smem_floats(D.m_u, D.m_z, D.z_jacobi)) * sizeof(float);
   if (wbytes > smem_optin) return fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", n_t, n_l);
@@ -1303,7 +1324,7 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
   sc.n = 1;
   sc.next_out = 0;
   if (s.exc == kPluck && s.pluck_amp != 0.0) {
-    const double c0 = s.pluck_amp / q.length_m, xp = s.pluck_pos;
+    const double c0 = s.pluck_amp / s.p.length_m, xp = s.pluck_pos;
     for (int l = 1; l < n_t; ++l) {
       const double x = static_cast<double>(l) / n_t;
       u[l - 1] = static_cast<float>(x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp));
@@ -1338,3 +1359,5 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
   if (rc == SFD_ENOCONV) return fail(rc, "coupled solve reached its sweep cap (result kept)");
   return SFD_OK;
 }
+
+#include "sfd_server.cuh"

@@ -44,6 +44,11 @@
 
 namespace sfd {
 
+// One resident block of up to 4 warps per SM lets each class use up to 255
+// registers.  Capping them at 168 or 128 (3 or 4 resident blocks) makes ptxas
+// spill 0.1-3 KB per thread and, measured on the 4096-string modulated
+// batch, lowers throughput from 124 M to 92 M / 88 M samples/s despite the
+// extra warps.
 __global__ void __launch_bounds__(128, 1) SFD_KERNEL(const Job* __restrict__ jobs, int n_jobs,
                                                     int* __restrict__ counter, int warp_floats) {
   extern __shared__ float smem[];

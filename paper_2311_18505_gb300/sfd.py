@@ -54,6 +54,30 @@ class sfd_excitation(ctypes.Structure):
 
 SFD_NOALLOC_SCRATCH_BYTES = 32 * 1024
 
+
+class sfd_request(ctypes.Structure):
+    _fields_ = [
+        ("params", sfd_string_params), ("exc", sfd_excitation),
+        ("mod_kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("mod_rate_hz", ctypes.c_double), ("mod_depth", ctypes.c_double),
+        ("mod_phase_rad", ctypes.c_double), ("mod_duration_s", ctypes.c_double),
+        ("n_samples", ctypes.c_int64), ("arrival_s", ctypes.c_double), ("tag", ctypes.c_uint64),
+    ]
+
+
+class sfd_chunk(ctypes.Structure):
+    _fields_ = [
+        ("tag", ctypes.c_uint64), ("first_sample", ctypes.c_int64), ("n", ctypes.c_int32),
+        ("last", ctypes.c_int32), ("status", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("samples", ctypes.POINTER(ctypes.c_float)), ("ready_s", ctypes.c_double), ("arrival_s", ctypes.c_double),
+    ]
+
+
+class sfd_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("queued", "live", "submitted", "admitted", "completed", "chunks",
+                                               "samples", "in_flight")] + \
+               [("pool_used", ctypes.c_uint64), ("pool_size", ctypes.c_uint64)]
+
 _lib = None
 
 
@@ -97,6 +121,12 @@ def lib() -> ctypes.CDLL:
         "sfd_ctx_kernel_times": (i32, [vp, P(ctypes.c_float), P(i32)]),
         "sfd_string_kernel_class": (i32, [vp, P(i32)]),
         "sfd_synthesize_noalloc": (i32, [ctypes.c_int, vp, P(sfd_string_params), P(sfd_excitation), i64, vp]),
+        "sfd_server_create": (i32, [vp, i32, i32, P(vp)]),
+        "sfd_server_submit": (i32, [vp, P(sfd_request)]),
+        "sfd_server_pump": (i32, [vp, P(P(sfd_chunk)), P(i32)]),
+        "sfd_server_clock": (dbl, [vp]),
+        "sfd_server_stats_get": (i32, [vp, P(sfd_server_stats)]),
+        "sfd_server_destroy": (i32, [vp]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -333,6 +363,63 @@ def sfd_synthesize_noalloc(device: int, stream, params: sfd_string_params, exc: 
     device allocation (scratch in the library's static device array)."""
     ptr = out_device if isinstance(out_device, int) else out_device.data_ptr()
     _check(lib().sfd_synthesize_noalloc(device, stream, ctypes.byref(params), ctypes.byref(exc), n_samples, ptr))
+
+
+# ------------------------------------------------------------ serving
+
+def sfd_server_create(ctx: int, chunk_samples: int = 1024, max_live: int = 4096) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().sfd_server_create(ctx, chunk_samples, max_live, ctypes.byref(out)))
+    return out.value
+
+
+def sfd_server_submit(sv: int, req: sfd_request) -> None:
+    _check(lib().sfd_server_submit(sv, ctypes.byref(req)))
+
+
+def sfd_server_pump(sv: int, copy: bool = True):
+    """One admission + launch + delivery round.  Returns a list of
+    (tag, first_sample, samples, last, status, ready_s, arrival_s); samples
+    is a numpy copy (copy=True) or the sample count (copy=False)."""
+    ptr = ctypes.POINTER(sfd_chunk)()
+    n = ctypes.c_int32()
+    _check(lib().sfd_server_pump(sv, ctypes.byref(ptr), ctypes.byref(n)))
+    res = []
+    for i in range(n.value):
+        c = ptr[i]
+        data = np.ctypeslib.as_array(c.samples, shape=(c.n,)).copy() if copy else c.n
+        res.append((c.tag, c.first_sample, data, bool(c.last), c.status, c.ready_s, c.arrival_s))
+    return res
+
+
+def sfd_server_clock(sv: int) -> float:
+    return lib().sfd_server_clock(sv)
+
+
+def sfd_server_stats_get(sv: int) -> sfd_server_stats:
+    st = sfd_server_stats()
+    _check(lib().sfd_server_stats_get(sv, ctypes.byref(st)))
+    return st
+
+
+def sfd_server_destroy(sv: int) -> None:
+    _check(lib().sfd_server_destroy(sv))
+
+
+def request_from_dict(d: dict, tag: int, n_samples: int | None = None, arrival_s: float = -1.0) -> sfd_request:
+    r = sfd_request()
+    r.params = params_from_dict(d)
+    r.exc = excitation_from_dict(d["excitation"])
+    mod = d.get("modulation", {"kind": "none"})
+    if mod.get("kind") == "vibrato":
+        r.mod_kind, r.mod_rate_hz, r.mod_depth, r.mod_phase_rad = SFD_MOD_VIBRATO, mod["rate"], mod["depth"], \
+            mod.get("phase", 0.0)
+    elif mod.get("kind") == "gliss":
+        r.mod_kind, r.mod_depth, r.mod_duration_s = SFD_MOD_GLISS, mod["depth"], mod["duration"]
+    r.n_samples = d["n_samples"] if n_samples is None else n_samples
+    r.arrival_s = arrival_s
+    r.tag = tag
+    return r
 
 
 # ------------------------------------------------------ dict marshalling

@@ -67,3 +67,33 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "sfd_oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes across the boundary has the C layout:
+    size and field offsets from a C program compiled against sfd.h."""
+    import shutil
+    import subprocess
+    from paper_2311_18505_gb300 import sfd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [sfd.sfd_string_params, sfd.sfd_excitation, sfd.sfd_request, sfd.sfd_chunk, sfd.sfd_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sfd.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln)}
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
