@@ -217,6 +217,9 @@ WORKLOAD_MODULATED = ("4096 strings x 4 s at 48 kHz, uneven N: f0 log-U[30,2000]
 
 
 def make_workload(args, rank):
+    if args.workload == "gradient":
+        base, _ = W.batch_gradient(64, seconds=0.5, seed=4 + 1000 * rank)
+        return base, WORKLOAD_GRADIENT
     if args.workload == "serving":
         trace = W.serving_trace(args.rate, args.trace_seconds, seed=5 + 1000 * rank)
         return [d for _, d in trace], WORKLOAD_SERVING.format(rate=args.rate, secs=args.trace_seconds,
@@ -540,13 +543,93 @@ def run_serving(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ gradients
+
+WORKLOAD_GRADIENT = ("differentiation: 64 plucked or hammered strings x 0.5 s at 48 kHz (seed 4), loss = sum of "
+                     "squared differences to targets rendered from parameters perturbed by up to 5 %, gradients "
+                     "w.r.t. kappa, alpha, sigma0, sigma1, amplitude; checkpoint every 1024 steps; one step = "
+                     "forward + adjoint")
+
+
+def run_gradient(args, ws, rank, local):
+    """Time forward synthesis plus the reverse sweep of the discrete adjoint
+    (segment replay from checkpoints + adjoint kernel) on the
+    differentiation workload."""
+    import torch
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    base, target = W.batch_gradient(64, seconds=0.5, seed=4 + 1000 * rank)
+    n = base[0]["n_samples"]
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 1 << 30)
+    # targets rendered by the same synthesis
+    hs = [sfd.string_from_dict(ctx, d) for d in target]
+    b = sfd.sfd_batch_create(ctx, hs)
+    ys, _ = sfd.sfd_batch_synthesize_host(b, [n] * len(target))
+    sfd.sfd_batch_destroy(b)
+    for h in hs:
+        sfd.sfd_string_destroy(h)
+    tgt = torch.from_numpy(np.stack(ys)).to(dev)
+    tape = sfd.sfd_tape_create(ctx, base, n, 1024)
+    y = torch.empty(len(base), n, device=dev, dtype=torch.float32)
+
+    def step():
+        t0 = time.perf_counter()
+        sfd.sfd_tape_forward(tape, y)
+        t1 = time.perf_counter()
+        dy = (2.0 * (y - tgt)).contiguous()
+        torch.cuda.synchronize(dev)
+        g = sfd.sfd_tape_backward(tape, dy, len(base))
+        t2 = time.perf_counter()
+        return g, t1 - t0, t2 - t1
+
+    for _ in range(args.warmup):
+        step()
+    barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    fw, bw, tot = [], [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize(dev)
+        g, a, c = step()
+        fw.append(a)
+        bw.append(c)
+        tot.append(a + c)
+    clk = clocks.stop()
+    sfd.sfd_tape_destroy(tape)
+    sfd.sfd_ctx_destroy(ctx)
+    t_step = max_over_ranks(ws, sum(tot) / len(tot))
+    if rank != 0:
+        return 0
+    samples = len(base) * n
+    line = {
+        "metric": METRIC, "value": ws * samples / t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (forward), f64 (adjoint recursion)", "data": "synthetic",
+        "config": {"workload": WORKLOAD_GRADIENT, "strings": len(base), "samples_per_string": n,
+                   "checkpoint_every": 1024, "timing": "host wall clock around the two C-ABI calls (each "
+                   "synchronises its stream)"},
+        "gradient": {"forward_ms": 1e3 * statistics.median(fw), "backward_ms": 1e3 * statistics.median(bw),
+                     "backward_over_forward": statistics.median(bw) / statistics.median(fw),
+                     "grad_finite": bool(np.all(np.isfinite(g)))},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: note requests per second")
     ap.add_argument("--trace-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--max-live", type=int, default=8192, help="serving: live-note slots")
@@ -568,6 +651,8 @@ def main(argv=None):
             return run_reference(args, ws, rank)
         if args.workload == "serving":
             return run_serving(args, ws, rank, local)
+        if args.workload == "gradient":
+            return run_gradient(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1:

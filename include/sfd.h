@@ -328,6 +328,34 @@ sfd_status sfd_server_stats_get(const sfd_server* sv, sfd_server_stats* st);
 /* Waits for any chunk in flight, frees every note and the buffers. */
 sfd_status sfd_server_destroy(sfd_server* sv);
 
+/* ---------------------------------------------------------------------
+ * Gradients of a waveform loss with respect to string parameters, by the
+ * discrete adjoint of the time-stepping (no counterpart in the paper).
+ *
+ * A tape holds n strings (params[i], exc[i]: pluck or hammer, no f0
+ * modulation) synthesized for n_samples each.  sfd_tape_forward writes the
+ * audio y (device, y[i * n_samples + j], metres) and keeps every string's
+ * state every checkpoint_every samples.  sfd_tape_backward takes dJ/dy
+ * (device, same layout) and writes, per string, dJ/d(kappa, alpha, sigma0,
+ * sigma1, amplitude) to grad[i * SFD_GRAD_PARAMS + k] (host): amplitude is
+ * the pluck amp_m, or the hammer vel_mps.  The gradient is that of the
+ * discrete scheme on the string's grid (N_t, N_l held fixed), through the
+ * FP32 trajectory the forward computed: each segment between checkpoints is
+ * replayed from its checkpoint and swept backwards by the adjoint kernel.
+ * The tape's own device memory (checkpoints, one segment's replay record,
+ * adjoint state) is allocated at create; the strings come from the ctx pool.
+ * --------------------------------------------------------------------- */
+typedef struct sfd_tape sfd_tape;
+#define SFD_GRAD_PARAMS 5
+sfd_status sfd_tape_create(sfd_ctx* ctx, int32_t n, const sfd_string_params* params, const sfd_excitation* exc,
+                           int64_t n_samples, int32_t checkpoint_every, sfd_tape** out);
+/* Runs from the initial state every time; returns SFD_EUNSTABLE / SFD_ENOCONV
+ * (audio written) if a string's synthesis reported one. */
+sfd_status sfd_tape_forward(sfd_tape* t, float* y_device);
+/* SFD_ESTATE before a forward. */
+sfd_status sfd_tape_backward(sfd_tape* t, const float* dy_device, double* grad);
+sfd_status sfd_tape_destroy(sfd_tape* t);
+
 /* Thread-local message describing the last error. */
 const char* sfd_last_error(void);
 

@@ -15,7 +15,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sfd.h"
+#include "sfd.h"
 #include "sfd_types.h"
 
 namespace sfd {
@@ -1361,3 +1361,4 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
 }
 
 #include "sfd_server.cuh"
+#include "sfd_tape.cuh"

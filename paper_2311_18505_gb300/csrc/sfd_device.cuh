@@ -13,11 +13,13 @@ namespace sfd {
 
 #define SFD_FULL 0xffffffffu
 
-struct Red {           // per-lane factors of the reduced (lane-boundary) system
-  float k1[5], k2[5];
-  float binv, cl;
+template <class T>
+struct RedT {          // per-lane factors of the reduced (lane-boundary) system
+  T k1[5], k2[5];
+  T binv, cl;
   int nlev;            // cyclic-reduction levels kept (warp-uniform)
 };
+using Red = RedT<float>;
 
 // Reciprocal for the eliminations: one MUFU instruction (rcp.approx.ftz,
 // about 1 ulp) instead of the IEEE sequence with its slow-path branch.  The
@@ -36,6 +38,13 @@ __device__ __forceinline__ float fast_rcp(float x) {
 // squares its coupling ratio at every level).
 constexpr float kPcrDrop = 7.4505806e-9f;   // 2^-27
 
+// reciprocal and reduction cut-off per precision (the FP64 instances serve
+// the adjoint sweep)
+__device__ __forceinline__ float rcp_of(float x) { return fast_rcp(x); }
+__device__ __forceinline__ double rcp_of(double x) { return 1.0 / x; }
+__device__ __forceinline__ float pcr_drop(float) { return kPcrDrop; }
+__device__ __forceinline__ double pcr_drop(double) { return 8.673617379884035e-19; }   // 2^-60
+
 // ----------------------------------------------------------------------------
 // Tridiagonal partition solver on a warp.  Row i: a_i x_{i-1} + b_i x_i +
 // c_i x_{i+1} = d_i.  On entry SUB = a, INV = b, CP = c for the lane's rows;
@@ -43,108 +52,109 @@ constexpr float kPcrDrop = 7.4505806e-9f;   // 2^-27
 // unknown, FF/GG = back-substitution weights of the lane's last unknown and
 // the previous lane's last unknown.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void tri_factor(const float* __restrict__ SUB, float* __restrict__ INV,
-                                           float* __restrict__ CP, float* __restrict__ AL,
-                                           float* __restrict__ FF, float* __restrict__ GG, int m,
-                                           int lane, Red& rd) {
+template <class T>
+__device__ __forceinline__ void tri_factor(const T* __restrict__ SUB, T* __restrict__ INV, T* __restrict__ CP,
+                                           T* __restrict__ AL, T* __restrict__ FF, T* __restrict__ GG, int m,
+                                           int lane, RedT<T>& rd) {
   const int base = lane * m;
-  float cprev = 0.f, alprev = 0.f;
+  T cprev = 0, alprev = 0;
   for (int r = 0; r < m; ++r) {
     const int i = base + r;
-    const float a = SUB[i], b = INV[i], c = CP[i];
-    float inv, al;
+    const T a = SUB[i], b = INV[i], c = CP[i];
+    T inv, al;
     if (r == 0) {
-      inv = fast_rcp(b);
+      inv = rcp_of(b);
       al = a * inv;
     } else {
-      inv = fast_rcp(b - a * cprev);
+      inv = rcp_of(b - a * cprev);
       al = -a * alprev * inv;
     }
-    const float cp = c * inv;
+    const T cp = c * inv;
     INV[i] = inv;
     CP[i] = cp;
     AL[i] = al;
     cprev = cp;
     alprev = al;
   }
-  float f = 1.f, g = 0.f;
-  FF[base + m - 1] = 1.f;
-  GG[base + m - 1] = 0.f;
+  T f = 1, g = 0;
+  FF[base + m - 1] = 1;
+  GG[base + m - 1] = 0;
   for (int r = m - 2; r >= 0; --r) {
     const int i = base + r;
-    const float cp = CP[i];
+    const T cp = CP[i];
     f = -cp * f;
     g = -AL[i] - cp * g;
     FF[i] = f;
     GG[i] = g;
   }
-  float f0n = __shfl_down_sync(SFD_FULL, FF[base], 1);
-  float g0n = __shfl_down_sync(SFD_FULL, GG[base], 1);
-  if (lane == kWarp - 1) { f0n = 0.f; g0n = 0.f; }
-  const float cl = CP[base + m - 1];
-  float A = AL[base + m - 1];
-  float B = 1.f + cl * g0n;
-  float C = cl * f0n;
+  T f0n = __shfl_down_sync(SFD_FULL, FF[base], 1);
+  T g0n = __shfl_down_sync(SFD_FULL, GG[base], 1);
+  if (lane == kWarp - 1) { f0n = 0; g0n = 0; }
+  const T cl = CP[base + m - 1];
+  T A = AL[base + m - 1];
+  T B = 1 + cl * g0n;
+  T C = cl * f0n;
   rd.cl = cl;
   rd.nlev = 5;
 #pragma unroll
-  for (int l = 0; l < 5; ++l) { rd.k1[l] = 0.f; rd.k2[l] = 0.f; }
+  for (int l = 0; l < 5; ++l) { rd.k1[l] = 0; rd.k2[l] = 0; }
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
-    if (__all_sync(SFD_FULL, fabsf(A) + fabsf(C) <= kPcrDrop * fabsf(B))) { rd.nlev = l; break; }
+    if (__all_sync(SFD_FULL, fabs(A) + fabs(C) <= pcr_drop(T(0)) * fabs(B))) { rd.nlev = l; break; }
     const int s = 1 << l;
-    float Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
-    float Cm = __shfl_up_sync(SFD_FULL, C, s);
-    float Ap = __shfl_down_sync(SFD_FULL, A, s), Bp = __shfl_down_sync(SFD_FULL, B, s);
-    float Cp = __shfl_down_sync(SFD_FULL, C, s);
-    if (lane < s) { Am = 0.f; Bm = 1.f; Cm = 0.f; }
-    if (lane + s >= kWarp) { Ap = 0.f; Bp = 1.f; Cp = 0.f; }
-    const float k1 = A * fast_rcp(Bm), k2 = C * fast_rcp(Bp);
+    T Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
+    T Cm = __shfl_up_sync(SFD_FULL, C, s);
+    T Ap = __shfl_down_sync(SFD_FULL, A, s), Bp = __shfl_down_sync(SFD_FULL, B, s);
+    T Cp = __shfl_down_sync(SFD_FULL, C, s);
+    if (lane < s) { Am = 0; Bm = 1; Cm = 0; }
+    if (lane + s >= kWarp) { Ap = 0; Bp = 1; Cp = 0; }
+    const T k1 = A * rcp_of(Bm), k2 = C * rcp_of(Bp);
     A = -Am * k1;
     C = -Cp * k2;
     B = B - Cm * k1 - Ap * k2;
     rd.k1[l] = k1;
     rd.k2[l] = k2;
   }
-  rd.binv = fast_rcp(B);
+  rd.binv = rcp_of(B);
 }
 
 // Solve in place: E holds d for the lane's rows on entry and x on exit.
-__device__ __forceinline__ void tri_solve(const float* __restrict__ SUB, const float* __restrict__ INV,
-                                          const float* __restrict__ CP, const float* __restrict__ FF,
-                                          const float* __restrict__ GG, float* __restrict__ E, int m,
-                                          int lane, const Red& rd) {
+template <class T>
+__device__ __forceinline__ void tri_solve(const T* __restrict__ SUB, const T* __restrict__ INV,
+                                          const T* __restrict__ CP, const T* __restrict__ FF,
+                                          const T* __restrict__ GG, T* __restrict__ E, int m, int lane,
+                                          const RedT<T>& rd) {
   const int base = lane * m;
-  float dp = 0.f;
+  T dp = 0;
   for (int r = 0; r < m; ++r) {
     const int i = base + r;
-    const float v = (r == 0) ? E[i] : E[i] - SUB[i] * dp;
+    const T v = (r == 0) ? E[i] : E[i] - SUB[i] * dp;
     dp = v * INV[i];
     E[i] = dp;
   }
-  const float dlast = dp;
-  float e = 0.f;
-  E[base + m - 1] = 0.f;
+  const T dlast = dp;
+  T e = 0;
+  E[base + m - 1] = 0;
   for (int r = m - 2; r >= 0; --r) {
     const int i = base + r;
     e = E[i] - CP[i] * e;
     E[i] = e;
   }
-  float e0n = __shfl_down_sync(SFD_FULL, E[base], 1);
-  if (lane == kWarp - 1) e0n = 0.f;
-  float D = dlast - rd.cl * e0n;
+  T e0n = __shfl_down_sync(SFD_FULL, E[base], 1);
+  if (lane == kWarp - 1) e0n = 0;
+  T D = dlast - rd.cl * e0n;
 #pragma unroll
   for (int l = 0; l < 5; ++l) {   // skipped levels carry zero multipliers
     const int s = 1 << l;
-    float Dm = __shfl_up_sync(SFD_FULL, D, s);
-    float Dp = __shfl_down_sync(SFD_FULL, D, s);
-    if (lane < s) Dm = 0.f;
-    if (lane + s >= kWarp) Dp = 0.f;
+    T Dm = __shfl_up_sync(SFD_FULL, D, s);
+    T Dp = __shfl_down_sync(SFD_FULL, D, s);
+    if (lane < s) Dm = 0;
+    if (lane + s >= kWarp) Dp = 0;
     D = D - rd.k1[l] * Dm - rd.k2[l] * Dp;
   }
-  const float X = D * rd.binv;
-  float Xp = __shfl_up_sync(SFD_FULL, X, 1);
-  if (lane == 0) Xp = 0.f;
+  const T X = D * rd.binv;
+  T Xp = __shfl_up_sync(SFD_FULL, X, 1);
+  if (lane == 0) Xp = 0;
   for (int r = 0; r < m; ++r) {
     const int i = base + r;
     E[i] = E[i] + FF[i] * X + GG[i] * Xp;

@@ -267,6 +267,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   }
   Scalars* scp = Dp->sc;
   int64_t n = scp->n, jnext = scp->next_out;
+  const int64_t n_first = n;
   float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w, scz = scp->scale_z, scx = scp->scale_x;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
@@ -725,6 +726,16 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
       __syncwarp();
       ++n;
+      if (job.traj) {   // replay for the adjoint: record the new level
+        float* rec = job.traj + (n - n_first - 1) * job.traj_stride;
+#pragma unroll
+        for (int r = 0; r < MU; ++r) {
+          const int i = ub + r;
+          if (i < n_u) { rec[i] = U[r]; rec[n_u + i] = DU[r]; }
+        }
+        for (int i = lane; i < n_z; i += kWarp) { rec[2 * n_u + i] = Z[i]; rec[2 * n_u + n_z + i] = DZ[i]; }
+        if (lane == 0) { rec[2 * n_u + 2 * n_z] = uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
+      }
     }
     float y;
     if (jnext == n - 1)

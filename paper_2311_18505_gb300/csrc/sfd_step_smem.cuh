@@ -65,6 +65,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   }
   Scalars* scp = Dp->sc;
   int64_t n = scp->n, jnext = scp->next_out;
+  const int64_t n_first = n;
   float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
@@ -410,6 +411,12 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
       if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
       __syncwarp();
       ++n;
+      if (job.traj) {   // replay for the adjoint: record the new level
+        float* rec = job.traj + (n - n_first - 1) * job.traj_stride;
+        for (int i = lane; i < n_u; i += kWarp) { rec[i] = U[i]; rec[n_u + i] = DU[i]; }
+        for (int i = lane; i < n_z; i += kWarp) { rec[2 * n_u + i] = Z[i]; rec[2 * n_u + n_z + i] = DZ[i]; }
+        if (lane == 0) { rec[2 * n_u + 2 * n_z] = uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
+      }
     }
     // output sample j = jnext: u^n or u^{n-1} (zeros once unstable)
     float y;

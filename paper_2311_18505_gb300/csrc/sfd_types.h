@@ -85,6 +85,34 @@ struct Job {
   const Desc* desc;
   float* out;             // first output sample of this job
   int64_t n_samples;
+  // optional trajectory record (gradient replay): after each step of the
+  // job, the new level's [u | D | z | Dz | u_H | D_H] at traj + k stride
+  // for the job's k-th step; nullptr: not recorded
+  float* traj;
+  int64_t traj_stride;
+};
+
+// One string's part of a reverse sweep of the discrete adjoint over the
+// levels (m_start, m_end] of a replayed segment (sfd_adjoint.cu).
+enum GradSlot : int {
+  kGLam2 = 0, kGMu2, kGS0u, kGS1, kGCa, kGCb, kGCz, kGLam2l, kGS0, kGS1l, kGAmp, kGradSlots
+};
+struct AdjJob {
+  const Desc* desc;            // coefficients and grid (the replayed string)
+  const float* u0;             // state at level m_start (a checkpoint): u, D, z, Dz
+  const float* du0;
+  const float* z0;
+  const float* dz0;
+  const Scalars* sc0;          // ... and u_H, D_H
+  const float* traj;           // levels m_start + 1 .. m_end (Job::traj layout)
+  int64_t traj_stride;
+  int64_t m_start, m_end;
+  const float* dy;             // dJ/dy for the string's samples (index = level)
+  double* adj;                 // adjoint of [u | D | z | Dz | u_H | D_H], level m_end in, m_start
+                               // out; then the warm starts of the two longitudinal solves (2 n_z)
+  double* grad;                // kGradSlots accumulators (raw coefficient gradients)
+  int32_t first;               // m_start == 1: add the level-1 and level-0 outputs, initial-state terms
+  float pluck_pos;             // peak of the pluck triangle (amplitude gradient), < 0: none
 };
 
 // Shared-memory words one warp needs for a string with row counts m_u, m_z.
@@ -97,6 +125,13 @@ inline __host__ __device__ int warp_smem_floats(int m_u, int m_z, int z_jacobi) 
   const int ru = kWarp * m_u + 4, rz = m_z > 0 ? kWarp * m_z + 4 : 0;
   if (m_u <= kMaxRegRows && (m_u & 1)) return 4 * ru + (z_jacobi ? 15 : 21) * rz;
   return kArraysU * ru + kArraysZ * rz;
+}
+
+// ... and the shared-memory bytes of the adjoint sweep: 17 FP64 and 9 FP32
+// (or int) transverse arrays, 13 FP64 and 6 FP32 longitudinal ones.
+inline __host__ __device__ int adj_smem_bytes(int m_u, int m_z) {
+  const int ru = kWarp * m_u + 4, rz = m_z > 0 ? kWarp * m_z + 4 : 0;
+  return (17 * 8 + 9 * 4) * ru + (13 * 8 + 6 * 4) * rz;
 }
 
 }  // namespace sfd

@@ -127,6 +127,10 @@ def lib() -> ctypes.CDLL:
         "sfd_server_clock": (dbl, [vp]),
         "sfd_server_stats_get": (i32, [vp, P(sfd_server_stats)]),
         "sfd_server_destroy": (i32, [vp]),
+        "sfd_tape_create": (i32, [vp, i32, P(sfd_string_params), P(sfd_excitation), i64, i32, P(vp)]),
+        "sfd_tape_forward": (i32, [vp, vp]),
+        "sfd_tape_backward": (i32, [vp, vp, P(dbl)]),
+        "sfd_tape_destroy": (i32, [vp]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -404,6 +408,39 @@ def sfd_server_stats_get(sv: int) -> sfd_server_stats:
 
 def sfd_server_destroy(sv: int) -> None:
     _check(lib().sfd_server_destroy(sv))
+
+
+# ------------------------------------------------------------ gradients
+
+SFD_GRAD_PARAMS = 5
+GRAD_PARAM_NAMES = ("kappa", "alpha", "sigma0", "sigma1", "amplitude")
+
+
+def sfd_tape_create(ctx: int, strings, n_samples: int, checkpoint_every: int = 1024) -> int:
+    """Tape of plucked or hammered strings (parameter dicts, no modulation)."""
+    n = len(strings)
+    params = (sfd_string_params * n)(*[params_from_dict(d) for d in strings])
+    excs = (sfd_excitation * n)(*[excitation_from_dict(d["excitation"]) for d in strings])
+    out = ctypes.c_void_p()
+    _check(lib().sfd_tape_create(ctx, n, params, excs, n_samples, checkpoint_every, ctypes.byref(out)))
+    return out.value
+
+
+def sfd_tape_forward(tape: int, y_device, allow_noconv: bool = False) -> None:
+    ptr = y_device if isinstance(y_device, int) else y_device.data_ptr()
+    _check(lib().sfd_tape_forward(tape, ptr), allow=(SFD_ENOCONV,) if allow_noconv else ())
+
+
+def sfd_tape_backward(tape: int, dy_device, n: int) -> np.ndarray:
+    """dJ/d(kappa, alpha, sigma0, sigma1, amplitude) per string, shape (n, 5)."""
+    ptr = dy_device if isinstance(dy_device, int) else dy_device.data_ptr()
+    g = np.zeros((n, SFD_GRAD_PARAMS), dtype=np.float64)
+    _check(lib().sfd_tape_backward(tape, ptr, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return g
+
+
+def sfd_tape_destroy(tape: int) -> None:
+    _check(lib().sfd_tape_destroy(tape))
 
 
 def request_from_dict(d: dict, tag: int, n_samples: int | None = None, arrival_s: float = -1.0) -> sfd_request:

@@ -1,0 +1,240 @@
+"""Gradients by the hand-written discrete adjoint (sfd_tape_*, grad.py), for
+plucked and hammered strings of the differentiation workload (loss: sum of
+squared differences to targets rendered from parameters perturbed by up to
+5 %):
+* the vector-Jacobian product with the GPU run's dJ/dy against the FP64
+  oracle (exactness of the adjoint, tight);
+* the loss gradient against central finite differences of the GPU
+  synthesis (relative steps 1e-3, 3e-3) and against the FP64 oracle's
+  gradient.  The loss of the FP32 run differs from the oracle's by the FP32
+  synthesis error, which is correlated with the output's sigma1
+  sensitivity, so those components are held relative to the string's
+  largest sensitivity."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_18505_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N_SHORT = 4800       # 0.1 s: five checkpoint segments of 1024, the last partial
+
+
+@pytest.fixture(scope="module")
+def sfd():
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd as S
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(sfd):
+    c = sfd.sfd_ctx_create(0, None, 512 << 20)
+    yield c
+    sfd.sfd_ctx_destroy(c)
+
+
+def workload(count, n):
+    base, target = W.batch_gradient(64, seconds=0.5, seed=4)
+    base = [dict(d, n_samples=n) for d in base[:count]]
+    target = [dict(d, n_samples=n) for d in target[:count]]
+    return base, target
+
+
+def targets_of(target, n):
+    ys, _ = oracle.run_batch(target, n_samples=n)
+    return np.stack(ys)
+
+
+def adjoint_grad(sfd, ctx, base, tgt, n, K=1024):
+    tape = sfd.sfd_tape_create(ctx, base, n, K)
+    try:
+        y = torch.empty(len(base), n, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        dy = 2.0 * (y.double() - torch.from_numpy(tgt).cuda())
+        g = sfd.sfd_tape_backward(tape, dy.float().contiguous(), len(base))
+        return g, y.cpu().numpy()
+    finally:
+        sfd.sfd_tape_destroy(tape)
+
+
+def perturbed(d, k, factor):
+    from paper_2311_18505_gb300.grad import params_of, with_params
+    r = np.array(params_of(d))
+    r[k] *= factor
+    return with_params(d, r)
+
+
+def gpu_losses(sfd, ctx, dicts, tgts, n):
+    hs = [sfd.string_from_dict(ctx, d) for d in dicts]
+    b = sfd.sfd_batch_create(ctx, hs)
+    try:
+        ys, _ = sfd.sfd_batch_synthesize_host(b, [n] * len(dicts))
+    finally:
+        sfd.sfd_batch_destroy(b)
+        grids = [sfd.sfd_string_info(h)[:2] for h in hs]
+        for h in hs:
+            sfd.sfd_string_destroy(h)
+    return [float(np.sum((y.astype(np.float64) - t) ** 2)) for y, t in zip(ys, tgts)], grids
+
+
+def test_tape_forward_is_the_plain_synthesis(sfd, ctx):
+    base, _ = workload(6, N_SHORT)
+    tape = sfd.sfd_tape_create(ctx, base, N_SHORT, 1024)
+    try:
+        y = torch.empty(len(base), N_SHORT, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        y = y.cpu().numpy()
+    finally:
+        sfd.sfd_tape_destroy(tape)
+    for d, row in zip(base, y):
+        s = sfd.string_from_dict(ctx, d)
+        assert np.array_equal(row, sfd.sfd_synthesize(s, N_SHORT))
+        sfd.sfd_string_destroy(s)
+
+
+def test_adjoint_matches_gpu_central_differences(sfd, ctx):
+    """Central differences of the GPU synthesis itself (relative steps 1e-3
+    and 3e-3).  FP32 rounding makes the difference quotient noisy where a
+    parameter barely moves the loss, so each component is held to the
+    spread of its two quotients plus 2 % (and the string's largest
+    sensitivity sets a floor)."""
+    base, target = workload(8, N_SHORT)
+    tgt = targets_of(target, N_SHORT)
+    g, _ = adjoint_grad(sfd, ctx, base, tgt, N_SHORT)
+    from paper_2311_18505_gb300.grad import params_of
+    steps = (1e-3, 3e-3)
+    dicts, tg = [], []
+    for i, d in enumerate(base):
+        for k in range(5):
+            for eps in steps:
+                for f in (1 + eps, 1 - eps):
+                    dicts.append(perturbed(d, k, f))
+                    tg.append(tgt[i])
+    losses, grids = gpu_losses(sfd, ctx, dicts, tg, N_SHORT)
+    _, base_grids = gpu_losses(sfd, ctx, base, list(tgt), N_SHORT)
+    checked = 0
+    for i, d in enumerate(base):
+        th = params_of(d)
+        sens = np.max(np.abs(g[i] * np.array(th)))
+        for k in range(5):
+            j = 20 * i + 4 * k
+            if any(grids[j + q] != base_grids[i] for q in range(4)):
+                continue   # the perturbation moved the grid: no derivative on a fixed grid
+            fd1 = (losses[j] - losses[j + 1]) / (2 * steps[0] * th[k])
+            fd3 = (losses[j + 2] - losses[j + 3]) / (2 * steps[1] * th[k])
+            band = 3 * abs(fd1 - fd3) + 2e-2 * abs(fd1) + 1e-3 * sens / abs(th[k])
+            assert abs(g[i, k] - fd1) <= band, (i, k, g[i, k], fd1, fd3)
+            checked += 1
+    assert checked >= 30
+
+
+def test_vector_jacobian_product_matches_the_oracle(sfd, ctx):
+    """The adjoint is the exact transpose of the step's linearisation: with
+    the residual weights w = dJ/dy of the GPU run, the adjoint's result must
+    equal d/dp sum_j w_j y_j(p) of the FP64 oracle (central differences,
+    relative step 1e-6, grid held fixed)."""
+    base, target = workload(8, N_SHORT)
+    tgt = targets_of(target, N_SHORT)
+    tape = sfd.sfd_tape_create(ctx, base, N_SHORT, 1024)
+    try:
+        y = torch.empty(len(base), N_SHORT, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        w = (2.0 * (y.double() - torch.from_numpy(tgt).cuda())).float().contiguous()
+        g = sfd.sfd_tape_backward(tape, w, len(base))
+    finally:
+        sfd.sfd_tape_destroy(tape)
+    w = w.double().cpu().numpy()
+    from paper_2311_18505_gb300.grad import params_of
+    for i, d in enumerate(base):
+        nt, nl = oracle.grid(d)
+        th = np.array(params_of(d))
+        runs = []
+        for k in range(5):
+            for f in (1 + 1e-6, 1 - 1e-6):
+                runs.append(dict(perturbed(d, k, f), n_t=nt, n_l=nl))
+        ys, _ = oracle.run_batch(runs, n_samples=N_SHORT)
+        ref = np.array([(w[i] @ ys[2 * k] - w[i] @ ys[2 * k + 1]) / (2e-6 * th[k]) for k in range(5)])
+        scale = np.max(np.abs(ref * th))
+        err = np.abs(g[i] - ref) * th
+        assert np.all(err <= 1e-4 * scale + 2e-3 * np.abs(ref * th)), (i, g[i], ref)
+
+
+def oracle_gradient(d, tgt, n, eps=1e-6):
+    """Central differences of the FP64 oracle's loss on the string's grid."""
+    from paper_2311_18505_gb300.grad import params_of
+    nt, nl = oracle.grid(d)
+    th = params_of(d)
+    runs = []
+    for k in range(5):
+        for f in (1 + eps, 1 - eps):
+            runs.append(dict(perturbed(d, k, f), n_t=nt, n_l=nl))
+    ys, _ = oracle.run_batch(runs, n_samples=n)
+    L = [float(np.sum((y - tgt) ** 2)) for y in ys]
+    return np.array([(L[2 * k] - L[2 * k + 1]) / (2 * eps * th[k]) for k in range(5)])
+
+
+def test_adjoint_matches_the_oracle_gradient(sfd, ctx):
+    base, target = workload(8, N_SHORT)
+    tgt = targets_of(target, N_SHORT)
+    g, _ = adjoint_grad(sfd, ctx, base, tgt, N_SHORT)
+    from paper_2311_18505_gb300.grad import params_of
+    for i, d in enumerate(base):
+        ref = oracle_gradient(d, tgt[i], N_SHORT)
+        th = np.array(params_of(d))
+        # each component against the string's largest relative sensitivity
+        scale = np.max(np.abs(ref * th))
+        err = np.abs(g[i] - ref) * th
+        assert np.all(err <= 2e-3 * scale + 1e-3 * np.abs(ref * th)), (i, g[i], ref)
+
+
+def test_gradient_does_not_depend_on_the_checkpoint_interval(sfd, ctx):
+    base, target = workload(6, N_SHORT)
+    tgt = targets_of(target, N_SHORT)
+    g1, y1 = adjoint_grad(sfd, ctx, base, tgt, N_SHORT, K=1024)
+    g2, y2 = adjoint_grad(sfd, ctx, base, tgt, N_SHORT, K=333)
+    g3, y3 = adjoint_grad(sfd, ctx, base, tgt, N_SHORT, K=N_SHORT)
+    assert np.array_equal(y1, y2) and np.array_equal(y1, y3)
+    # the replayed levels and the adjoint recursion are identical; only the
+    # grouping of the FP64 gradient sums differs
+    np.testing.assert_allclose(g2, g1, rtol=1e-9, atol=0)
+    np.testing.assert_allclose(g3, g1, rtol=1e-9, atol=0)
+
+
+def test_autograd_function_and_a_descent_step(sfd, ctx):
+    from paper_2311_18505_gb300 import grad as G
+    base, target = workload(6, N_SHORT)
+    tgt = torch.from_numpy(targets_of(target, N_SHORT)).cuda()
+    theta = torch.tensor(G.theta_of(base), dtype=torch.float64, requires_grad=True)
+    y = G.synthesize(theta, base, N_SHORT, ctx)
+    loss = ((y.double() - tgt) ** 2).sum()
+    loss.backward()
+    g_direct, _ = adjoint_grad(sfd, ctx, base, tgt.cpu().numpy(), N_SHORT)
+    np.testing.assert_allclose(theta.grad.numpy(), g_direct, rtol=1e-6)
+    # a small step against the gradient (scaled per parameter) lowers the loss
+    with torch.no_grad():
+        step = -1e-3 * theta * torch.sign(theta.grad)
+        y2 = G.synthesize(theta + step, base, N_SHORT, ctx)
+        loss2 = ((y2.double() - tgt) ** 2).sum()
+    assert float(loss2) < float(loss)
+
+
+def test_full_differentiation_workload_against_the_oracle(sfd, ctx):
+    """64 strings x 0.5 s, checkpoint every 1024 steps; four strings checked
+    against the oracle gradient at full length."""
+    n = 24000
+    base, target = workload(64, n)
+    tgt = targets_of(target, n)
+    g, y = adjoint_grad(sfd, ctx, base, tgt, n, K=1024)
+    assert np.all(np.isfinite(g)) and np.all(np.isfinite(y))
+    from paper_2311_18505_gb300.grad import params_of
+    for i in (0, 17, 33, 63):
+        ref = oracle_gradient(base[i], tgt[i], n)
+        th = np.array(params_of(base[i]))
+        scale = np.max(np.abs(ref * th))
+        err = np.abs(g[i] - ref) * th
+        assert np.all(err <= 5e-3 * scale + 2e-3 * np.abs(ref * th)), (i, g[i], ref)

@@ -104,7 +104,7 @@ def test_served_notes_equal_alone(sfd):
 
 def server_reservation(max_live: int, chunk: int) -> int:
     rnd = lambda n: (n + 255) // 256 * 256
-    return 2 * (rnd(4 * max_live * chunk) + rnd(24 * max_live))   # output rows + job table
+    return 2 * (rnd(4 * max_live * chunk) + rnd(40 * max_live))   # output rows + job table (40 B jobs)
 
 
 def test_admission_by_device_memory(sfd):
