@@ -231,10 +231,12 @@ def test_pool_exhaustion_is_enomem(sfd):
         sfd.sfd_ctx_destroy(c)
 
 
-def test_full_batch_sampled_parity(sfd, ctx):
+def test_full_batch_parity(sfd, ctx):
     """The 256-string, 2 s mixed batch in the benchmark's launch configuration:
-    sampled strings' first 0.25 s against the oracle (bowed strings: 150
-    samples), every output finite."""
+    the first 0.25 s of every plucked or struck string against the oracle
+    within 1e-4, or, where FP32 storage of the state alone moves the oracle
+    further (strongly nonlinear strings struck hard), within three times that
+    floor; the first 150 samples of every bowed string; every output finite."""
     strings = W.batch_mixed(256, seconds=2.0, seed=2)
     hs = [sfd.string_from_dict(ctx, d) for d in strings]
     b = sfd.sfd_batch_create(ctx, hs)
@@ -249,11 +251,16 @@ def test_full_batch_sampled_parity(sfd, ctx):
     y = out.cpu().numpy()
     assert np.all(np.isfinite(y))
     assert np.all(st == 0)
-    # largest grids, every excitation kind, spread of alpha
-    sizes = [oracle.grid(d)[0] + oracle.grid(d)[1] for d in strings]
-    pick = set(np.argsort(sizes)[-3:].tolist()) | {0, 1, 2, 3, 50, 100, 150, 200, 255}
-    for i in sorted(pick):
-        d = strings[i]
-        n = 150 if d["excitation"]["kind"] == "bow" else 12000
-        ref = oracle.run(d, n)
-        assert rel_l2(y[offs[i]:offs[i] + n], ref) <= (1e-3 if n == 150 else TOL), i
+    lens = [150 if d["excitation"]["kind"] == "bow" else 12000 for d in strings]
+    refs, _ = oracle.run_batch(strings, n_samples=lens)
+    from fp32_floor import fp32_state_floor
+    beyond = []
+    for i, (n, ref) in enumerate(zip(lens, refs)):
+        e = rel_l2(y[offs[i]:offs[i] + n], ref)
+        if n == 150:
+            assert e <= 1e-3, (i, e)
+        elif e > TOL:
+            floor = fp32_state_floor(strings[i], n)
+            assert floor > TOL and e <= 3 * floor, (i, e, floor)
+            beyond.append(i)
+    assert len(beyond) <= 3, beyond   # 2 of the 160 plucked or struck strings
