@@ -47,6 +47,7 @@ class Spec(ctypes.Structure):
         ("mod_kind", ctypes.c_int32), ("pad1", ctypes.c_int32),
         ("mod_rate", ctypes.c_double), ("mod_depth", ctypes.c_double),
         ("mod_phase", ctypes.c_double), ("mod_duration", ctypes.c_double),
+        ("out_channel", ctypes.c_int32), ("pad2", ctypes.c_int32),
     ]
 
 
@@ -117,6 +118,7 @@ def spec(d: dict, n_t: int = 0, n_l: int = 0) -> Spec:
     mod = d.get("modulation", {"kind": "none"})
     s.gamma_max_ratio = d.get("gamma_max_ratio", gamma_max_ratio(mod))
     s.pickup = d.get("pickup", 0.7)
+    s.out_channel = 1 if d.get("output", "transverse") == "longitudinal" else 0
     ex = d["excitation"]
     s.exc_kind = EXC[ex["kind"]]
     if ex["kind"] == "pluck":

@@ -46,6 +46,7 @@ struct sfdo_string {
   /* excitation point interpolation (Sec. 3.3: I_p, J_p with p = 1)          */
   int e_node[2]; double e_w[2];
   int o_node[2]; double o_w[2];
+  int ol_node[2]; double ol_w[2];   /* pickup on the longitudinal grid */
   double last_power, last_G, last_v, last_F, last_resid;
 };
 
@@ -321,6 +322,14 @@ sfdo_string* sfdo_create(const sfdo_spec* s) {
   build_overlaps(S);
   build_ordering(S);
   interp_weights(S, s->pickup, S->o_node, S->o_w);
+  {   /* the same linear interpolation on the longitudinal nodes */
+    double pos = s->pickup * nl;
+    int m = (int)floor(pos);
+    if (m < 0) m = 0;
+    if (m > nl - 1) m = nl - 1;
+    S->ol_node[0] = m; S->ol_w[0] = 1.0 - (pos - m);
+    S->ol_node[1] = m + 1; S->ol_w[1] = pos - m;
+  }
   if (s->exc_kind == SFDO_EXC_HAMMER) interp_weights(S, s->ham_pos, S->e_node, S->e_w);
   else if (s->exc_kind == SFDO_EXC_BOW) interp_weights(S, s->bow_pos, S->e_node, S->e_w);
   /* band width from the sparsity of the assembled system (all strains set
@@ -645,7 +654,8 @@ static int step(sfdo_string* S) {
   return 0;
 }
 
-/* Output sample y^j = L I(x_o) u^j, j = 0, 1, 2, ... (reading A10). */
+/* Output sample y^j = L I(x_o) u^j, j = 0, 1, 2, ... (reading A10), or the
+ * longitudinal displacement at the pickup (out_channel 1). */
 int sfdo_run(sfdo_string* S, int64_t n, double* y) {
   if (!S || n < 0) return -1;
   for (int64_t s = 0; s < n; ++s) {
@@ -654,8 +664,13 @@ int sfdo_run(sfdo_string* S, int64_t n, double* y) {
       int rc = step(S);
       if (rc) return rc;
     }
-    const double* src = (j == S->n) ? S->u : S->up;
-    y[s] = S->p.length * interp(S, src, S->o_node, S->o_w);
+    if (S->p.out_channel == 1) {   /* longitudinal displacement at the pickup (Sec. 4.2) */
+      const double* zs = (j == S->n) ? S->z : S->zp;
+      y[s] = S->p.length * (S->ol_w[0] * Z(S, zs, S->ol_node[0]) + S->ol_w[1] * Z(S, zs, S->ol_node[1]));
+    } else {
+      const double* src = (j == S->n) ? S->u : S->up;
+      y[s] = S->p.length * interp(S, src, S->o_node, S->o_w);
+    }
     S->next_out++;
   }
   return 0;

@@ -76,6 +76,8 @@ typedef struct {
   double mod_depth;       /* vibrato depth [cents] / glissando span [octaves]   */
   double mod_phase;       /* vibrato phase [rad]                                */
   double mod_duration;    /* glissando duration [s]                             */
+  int32_t out_channel;    /* 0: transverse u, 1: longitudinal zeta (Sec. 4.2)   */
+  int32_t pad2;
 } sfdo_spec;
 
 typedef struct sfdo_string sfdo_string;
@@ -88,7 +90,9 @@ int sfdo_grid(const sfdo_spec* s, int32_t* n_t, int32_t* n_l);
 sfdo_string* sfdo_create(const sfdo_spec* s);
 void sfdo_destroy(sfdo_string* st);
 
-/* Append n output samples y^j = L * I(x_o) u^j, j = next index ... to y.
+/* Append n output samples y^j = L * I(x_o) u^j (out_channel 1: the
+ * longitudinal L * I_l(x_o) zeta^j on the longitudinal grid), j = next
+ * index ... to y.
  * Returns 0, or a negative code if the state became non-finite. */
 int sfdo_run(sfdo_string* st, int64_t n, double* y);
 

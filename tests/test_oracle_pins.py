@@ -377,6 +377,65 @@ def test_longitudinal_motion_quadratic_in_amplitude():
     assert zs[1] / zs[0] == pytest.approx(4.0, rel=1e-3)
 
 
+# ------------------------------------------- longitudinal output channel
+
+def test_longitudinal_output_zero_at_alpha_one():
+    for ex in EXCS:
+        y = oracle.run(W.make(alpha=1.0, excitation=ex, output="longitudinal"), 2000)
+        assert np.all(y == 0.0)
+
+
+def test_longitudinal_output_reads_zeta_at_the_pickup():
+    """The sample is L times the linear interpolation of zeta^j at x_o on
+    the longitudinal grid (nodes m h_l, fixed ends)."""
+    d = W.make(alpha=3.0, excitation={"kind": "pluck", "amp": 5e-3, "pos": 0.3}, pickup=0.63,
+               output="longitudinal")
+    _, n_l = oracle.grid(d)
+    s = oracle.OracleString(d)
+    for n in (1, 7, 500):
+        y = s.run(n)
+        _, _, _, z, _ = s.state()
+        node = np.concatenate([[0.0], z, [0.0]])          # node values zeta_0 .. zeta_{N_l}
+        want = d["length"] * np.interp(0.63, np.arange(n_l + 1) / n_l, node)
+        assert y[-1] == pytest.approx(want, rel=1e-13, abs=1e-300)
+
+
+def test_longitudinal_output_antisymmetric_under_mirror():
+    """(x_P, x_o) -> (1 - x_P, 1 - x_o) mirrors the string: u keeps its sign,
+    the longitudinal displacement changes it."""
+    a = W.make(alpha=3.0, excitation={"kind": "pluck", "amp": 5e-3, "pos": 0.3}, pickup=0.7,
+               output="longitudinal")
+    b = W.make(alpha=3.0, excitation={"kind": "pluck", "amp": 5e-3, "pos": 0.7}, pickup=0.3,
+               output="longitudinal")
+    ya, yb = oracle.run(a, 4000), oracle.run(b, 4000)
+    assert np.max(np.abs(ya)) > 0
+    assert np.max(np.abs(ya + yb)) <= 1e-12 * np.max(np.abs(ya))
+
+
+def test_longitudinal_output_quadratic_in_amplitude():
+    ys = [oracle.run(W.make(alpha=3.0, excitation={"kind": "hammer", "mass": 5e-3, "vel": v,
+                                                     "pos": 0.2, "omega": 3000.0, "alpha": 1.0},
+                            output="longitudinal"), 2000) for v in (1e-3, 2e-3)]
+    assert np.max(np.abs(ys[1] - 4 * ys[0])) <= 1e-3 * np.max(np.abs(ys[1]))
+
+
+@pytest.mark.parametrize("kappa,c0", [(6.08, 0.0078), (9.63, 0.0085)])
+def test_longitudinal_spectrum_fig2(kappa, c0):
+    """Sec. 4.2 / Fig. 2 (f0 = 300 Hz, alpha = 3, x_P = 0.14, lossless): zeta
+    is forced by the square of the transverse strain, so its strongest
+    component lies at the sum f_1 + f_2 of the first two transverse partials
+    (near the longitudinal fundamental alpha f0 = 900 Hz), and it is far
+    weaker than u."""
+    d = W.make(f0=300.0, alpha=3.0, kappa=kappa, sigma0=0.0, sigma1=0.0,
+               excitation={"kind": "pluck", "amp": c0, "pos": 0.14}, n_samples=24000)
+    yu = oracle.run(d)
+    yz = oracle.run(dict(d, output="longitudinal"))
+    f1 = peak_frequency(yu, d["fs"], 200.0, 400.0)
+    f2 = peak_frequency(yu, d["fs"], 500.0, 700.0)
+    assert peak_frequency(yz, d["fs"], 100.0, 2000.0) == pytest.approx(f1 + f2, abs=0.5)
+    assert np.std(yz) < 0.2 * np.std(yu)
+
+
 def test_pitch_rises_with_amplitude():
     """Tension modulation (the '+' sign of Eq. 4): a loud pluck of a string
     with alpha > 1 sounds sharper than a soft one."""
