@@ -59,6 +59,11 @@ enum {
 enum { SFD_BOUNDARY_CLAMPED = 0, SFD_BOUNDARY_SIMPLY_SUPPORTED = 1 };
 enum { SFD_GRID_THETA_BOUND = 0, SFD_GRID_PRINTED = 1 };
 enum { SFD_MOD_NONE = 0, SFD_MOD_VIBRATO = 1, SFD_MOD_GLISS = 2 };
+/* What the output samples read at the pickup (Sec. 4.2, Fig. 2 shows the
+ * spectra of both): the transverse displacement L u(x_o) or the
+ * longitudinal displacement L zeta(x_o), each linearly interpolated on its
+ * own grid.  Strings with alpha = 1 have zeta = 0. */
+enum { SFD_OUTPUT_TRANSVERSE = 0, SFD_OUTPUT_LONGITUDINAL = 1 };
 
 typedef struct sfd_ctx sfd_ctx;
 typedef struct sfd_string sfd_string;
@@ -84,11 +89,14 @@ typedef struct {
                              h_t of Sec. 3.2, which is that bound for theta = 1   */
   double pickup_pos;      /* output point, fraction of L, default 0.7             */
   double f0_max_ratio;    /* >= 1: grids sized for gamma * ratio (modulation peak) */
+  int32_t output;         /* SFD_OUTPUT_*, default transverse; anything else:
+                             SFD_EINVAL.  sfd_tape_create accepts transverse only */
+  int32_t pad_;
 } sfd_string_params;
 
 /* Fill p with the defaults (f0 = 110, kappa = 1, alpha = 1, sigma0 = 0.5,
  * sigma1 = 1e-5, L = 1 m, fs = 48 kHz, rho A = 5e-3, theta = (1+4/pi^2)/2,
- * clamped, theta-bound grid, pickup 0.7, ratio 1). */
+ * clamped, theta-bound grid, pickup 0.7, ratio 1, transverse output). */
 void sfd_params_default(sfd_string_params* p);
 
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t

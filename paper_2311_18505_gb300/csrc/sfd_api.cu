@@ -326,6 +326,8 @@ void fill_desc(sfd_string* s) {
   D.cz = static_cast<float>(phi * k * k / (2.0 * ht * ht * hl));
   D.out_scale = static_cast<float>(p.length_m);
   point_weights(s->n_t, p.pickup_pos, &D.o_node, &D.o_w);
+  D.out_ch = p.output;
+  point_weights(s->n_l, p.pickup_pos, &D.ol_node, &D.ol_w);
   D.jscale = static_cast<float>(s->n_t * rho);
   // The FP32 factorisation of the transverse matrix is itself a lasting
   // perturbation of the same size.  Strings of at most 31 unknowns (f0
@@ -427,6 +429,8 @@ sfd_status normalize_params(sfd_string_params& q, double* gamma_out) {
   if (!(q.length_m > 0) || !(q.linear_density > 0)) return fail(SFD_EINVAL, "length and density must be > 0");
   if (q.boundary != 0 && q.boundary != 1) return fail(SFD_EINVAL, "bad boundary");
   if (q.grid_rule != 0 && q.grid_rule != 1) return fail(SFD_EINVAL, "bad grid rule");
+  if (q.output != SFD_OUTPUT_TRANSVERSE && q.output != SFD_OUTPUT_LONGITUDINAL)
+    return fail(SFD_EINVAL, "bad output channel");
   *gamma_out = gamma;
   return SFD_OK;
 }

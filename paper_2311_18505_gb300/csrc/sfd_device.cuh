@@ -185,6 +185,14 @@ __device__ __forceinline__ float interp2(const float* __restrict__ A, int node, 
   return (1.f - w) * A[node - 1] + w * A[node];
 }
 
+// The same interpolation on the longitudinal grid (nodes 0..N_l, rows
+// node - 1): the fixed ends and rows past n_z read zero.
+__device__ __forceinline__ float zinterp(const float* __restrict__ A, int node, float w, int n_z) {
+  const float a = (node >= 1 && node - 1 < n_z) ? A[node - 1] : 0.f;
+  const float b = (node >= 0 && node < n_z) ? A[node] : 0.f;
+  return (1.f - w) * a + w * b;
+}
+
 // Bow friction: solve v + c phi(v) = b with phi(v) = sign(v)(eps + (1-eps)
 // e^{-a|v|}) (Sec. 3.3.1, Eq. 5).  Sticking (v = 0, phi = b/c) whenever
 // |b| <= c; otherwise the root of the convex g(w) = w + c phi(w) - |b| on

@@ -442,8 +442,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     for (int r = 0; r < MU; ++r) x[r] += rr[r];
   };
 
-  const int on = Dp->o_node;
-  const float ow = Dp->o_w, oscale = Dp->out_scale;
+  const int on = Dp->o_node, oln = Dp->ol_node;
+  const float ow = Dp->o_w, olw = Dp->ol_w, oscale = Dp->out_scale;
+  const bool zout = Dp->out_ch == 1;
   const int64_t j_end = jnext + job.n_samples;
   float outbuf = 0.f;
   int64_t opos = 0;
@@ -738,10 +739,17 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       }
     }
     float y;
-    if (jnext == n - 1)
+    if (zout) {   // L zeta^j at the pickup (zero without a longitudinal grid)
+      y = 0.f;
+      if (has_z) {
+        y = zinterp(Z, oln, olw, n_z);
+        if (jnext == n - 1) y -= zinterp(DZ, oln, olw, n_z);
+      }
+    } else if (jnext == n - 1) {
       y = node_interp<MU>(U, on, ow, n_u) - node_interp<MU>(DU, on, ow, n_u);
-    else
+    } else {
       y = node_interp<MU>(U, on, ow, n_u);
+    }
     y *= oscale;
     if (status & kStUnstable) y = 0.f;
     if ((opos & (kWarp - 1)) == lane) outbuf = y;

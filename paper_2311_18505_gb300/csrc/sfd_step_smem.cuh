@@ -191,8 +191,9 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
     }
   };
 
-  const int on = Dp->o_node;
-  const float ow = Dp->o_w, oscale = Dp->out_scale;
+  const int on = Dp->o_node, oln = Dp->ol_node;
+  const float ow = Dp->o_w, olw = Dp->ol_w, oscale = Dp->out_scale;
+  const bool zout = Dp->out_ch == 1;
   const int64_t j_end = jnext + job.n_samples;
   float outbuf = 0.f;
   int64_t opos = 0;
@@ -418,12 +419,19 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         if (lane == 0) { rec[2 * n_u + 2 * n_z] = uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
       }
     }
-    // output sample j = jnext: u^n or u^{n-1} (zeros once unstable)
+    // output sample j = jnext: u^n or u^{n-1}, or zeta (zeros once unstable)
     float y;
-    if (jnext == n - 1)
+    if (zout) {
+      y = 0.f;
+      if (has_z) {
+        y = zinterp(Z, oln, olw, n_z);
+        if (jnext == n - 1) y -= zinterp(DZ, oln, olw, n_z);
+      }
+    } else if (jnext == n - 1) {
       y = interp2(U, on, ow) - interp2(DU, on, ow);
-    else
+    } else {
       y = interp2(U, on, ow);
+    }
     y *= oscale;
     if (status & kStUnstable) y = 0.f;
     if ((opos & (kWarp - 1)) == lane) outbuf = y;

@@ -50,6 +50,9 @@ struct Desc {
   float out_scale;        // L (output in metres)
   int32_t o_node;         // pickup: nodes o_node, o_node + 1 (0..N_t)
   float o_w;              //   weight of o_node + 1
+  int32_t out_ch;         // 0: L u at the pickup, 1: L zeta at the pickup
+  int32_t ol_node;        // pickup on the longitudinal grid: nodes ol_node, ol_node + 1 (0..N_l)
+  float ol_w;             //   weight of ol_node + 1
   int32_t e_node;         // excitation point, same convention
   float e_w;
   float jscale;           // J = I / h_t

@@ -24,6 +24,8 @@ SFD_ECUDA, SFD_ETIMEOUT, SFD_EBUSY, SFD_ESTATE = -5, -6, -7, -8
 STATUS_NAMES = {0: "SFD_OK", -1: "SFD_EINVAL", -2: "SFD_ENOMEM", -3: "SFD_EUNSTABLE", -4: "SFD_ENOCONV",
                 -5: "SFD_ECUDA", -6: "SFD_ETIMEOUT", -7: "SFD_EBUSY", -8: "SFD_ESTATE"}
 SFD_MOD_NONE, SFD_MOD_VIBRATO, SFD_MOD_GLISS = 0, 1, 2
+SFD_OUTPUT_TRANSVERSE, SFD_OUTPUT_LONGITUDINAL = 0, 1
+OUTPUTS = {"transverse": SFD_OUTPUT_TRANSVERSE, "longitudinal": SFD_OUTPUT_LONGITUDINAL}
 
 
 class SfdError(RuntimeError):
@@ -39,6 +41,7 @@ class sfd_string_params(ctypes.Structure):
         ("length_m", ctypes.c_double), ("fs", ctypes.c_double), ("linear_density", ctypes.c_double),
         ("theta", ctypes.c_double), ("boundary", ctypes.c_int32), ("grid_rule", ctypes.c_int32),
         ("pickup_pos", ctypes.c_double), ("f0_max_ratio", ctypes.c_double),
+        ("output", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 
@@ -475,6 +478,7 @@ def params_from_dict(d: dict) -> sfd_string_params:
     p.boundary = d.get("boundary", 0)
     p.grid_rule = d.get("grid_rule", 0)
     p.pickup_pos = d.get("pickup", 0.7)
+    p.output = OUTPUTS[d.get("output", "transverse")]
     mod = d.get("modulation", {"kind": "none"})
     ratio = 1.0
     if mod.get("kind") == "vibrato":

@@ -97,3 +97,33 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (compiled with the host C compiler; no GPU)."""
+    import shutil
+    import subprocess
+    from paper_2311_18505_gb300 import sfd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"sfd_string_params": sfd.sfd_string_params, "sfd_excitation": sfd.sfd_excitation,
+               "sfd_request": sfd.sfd_request, "sfd_chunk": sfd.sfd_chunk,
+               "sfd_server_stats": sfd.sfd_server_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sfd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                   text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
