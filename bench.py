@@ -623,7 +623,7 @@ def run_gradient(args, ws, rank, local):
     return 0
 
 
-def main(argv=None):
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -644,7 +644,11 @@ def main(argv=None):
     ap.add_argument("--cpu-samples", type=int, default=96000)
     ap.add_argument("--ref-strings", type=int, default=128)
     ap.add_argument("--ref-samples", type=int, default=96000)
-    args = ap.parse_args(argv)
+    return ap.parse_args(argv)
+
+
+def main(argv=None):
+    args = parse_args(argv)
     ws, rank, local = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

@@ -272,7 +272,10 @@ def sfd_batch_synthesize(b: int, n_samples, out_device, out_offsets, per_string_
     return st
 
 
-def sfd_batch_synthesize_host(b: int, n_samples, out_offsets=None, allow_noconv: bool = False):
+def sfd_batch_synthesize_host(b: int, n_samples, out_offsets=None, allow_noconv: bool = False,
+                              check: bool = True):
+    """Host output: (list of per-string sample arrays, per-string status).
+    With check=False a string's failure is reported in the status only."""
     ns = np.ascontiguousarray(n_samples, dtype=np.int64)
     if out_offsets is None:
         offs = np.zeros(len(ns), dtype=np.int64)
@@ -285,7 +288,7 @@ def sfd_batch_synthesize_host(b: int, n_samples, out_offsets=None, allow_noconv:
     _check(lib().sfd_batch_synthesize_host(b, _i64p(ns), out.ctypes.data, _i64p(offs),
                                            st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
     bad = [int(x) for x in st if x != SFD_OK and not (allow_noconv and x == SFD_ENOCONV)]
-    if bad:
+    if bad and check:
         raise SfdError(bad[0], f"{len(bad)} string(s) reported {STATUS_NAMES.get(bad[0])}")
     return [out[o:o + n] for o, n in zip(offs, ns)], st
 

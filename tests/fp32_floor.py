@@ -28,3 +28,32 @@ def fp32_state_floor(d: dict, n: int) -> float:
         s.set_state(u32 - d32, u32, z32 - dz32, z32)
     y = np.asarray(y)
     return float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+
+
+def coefficient_floor(d: dict, n: int) -> float:
+    """Largest rel-L2 change over n samples when one of f0, alpha, kappa,
+    sigma0, sigma1 moves by 2^-24 relative (the rounding of an FP64 value to
+    FP32), on the string's own grid.  The kernel's coefficients are FP32
+    roundings of FP64 expressions in these parameters, so this is the
+    problem's own conditioning at FP32 input precision.  It is large for the
+    longitudinal output when a sum of transverse partials lies near a
+    longitudinal mode (a near resonance of the forced zeta)."""
+    n_t, n_l = oracle.grid(d)
+    ref = oracle.run(d, n)
+    norm = np.linalg.norm(ref)
+    if norm == 0:
+        return 0.0
+    worst = 0.0
+    for key in ("f0", "alpha", "kappa", "sigma0", "sigma1"):
+        if d[key] == 0:
+            continue
+        p = dict(d, n_t=n_t, n_l=n_l)
+        p[key] = d[key] * (1.0 + 2.0 ** -24)
+        worst = max(worst, float(np.linalg.norm(oracle.run(p, n) - ref) / norm))
+    return worst
+
+
+def fp32_floor(d: dict, n: int) -> float:
+    """FP32 state storage plus FP32 coefficient rounding (both measured with
+    the oracle)."""
+    return fp32_state_floor(d, n) + coefficient_floor(d, n)

@@ -4,15 +4,19 @@ spectrum), through the C-ABI against the FP64 oracle.
 
 zeta is a second-order quantity driven by the square of the transverse
 strain, so a relative error of the transverse state shows up about twice in
-it; the bar is the transverse one (rel-L2 <= 1e-4 over the run) unless the
-oracle with its state rounded to FP32 already departs further (the FP32
-storage floor), in which case the kernel must stay within 3x that floor."""
+it.  It is also ill-conditioned where a sum of transverse partials lies near
+a longitudinal mode: the forced response then moves by ~1e-4 for a 2^-24
+relative change of f0 or alpha.  The bar is the transverse one (rel-L2 <=
+1e-4 over the run) unless the oracle itself moves further under FP32
+precision -- its state rounded to FP32 after every step plus the largest
+change from rounding one parameter to FP32 (fp32_floor) -- in which case
+the kernel must stay within 3x that floor."""
 
 import numpy as np
 import pytest
 
 import oracle
-from fp32_floor import fp32_state_floor
+from fp32_floor import fp32_floor
 from paper_2311_18505_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -82,7 +86,7 @@ def test_longitudinal_parity(sfd, ctx, name):
     assert np.max(np.abs(ref)) > 0
     e = rel_l2(y, ref)
     if e > TOL:
-        floor = fp32_state_floor(d, d["n_samples"])
+        floor = fp32_floor(d, d["n_samples"])
         assert e <= 3 * floor, (name, e, floor)
 
 
@@ -132,7 +136,7 @@ def test_mixed_channels_in_one_batch(sfd, ctx):
     for i in picks:
         ref = oracle.run(strings[i])
         e = rel_l2(ys[i], ref)
-        assert e <= TOL or e <= 3 * fp32_state_floor(strings[i], strings[i]["n_samples"]), (i, e)
+        assert e <= TOL or e <= 3 * fp32_floor(strings[i], strings[i]["n_samples"]), (i, e)
 
 
 def test_invalid_channel_and_tape_refusal(sfd, ctx):
