@@ -230,20 +230,15 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   // ---- shared memory: transverse transfer arrays, then the longitudinal grid ----
   float* p = wbase;
   auto U_ = [&]() { float* a = p + 2; p += RU; return a; };
-  float *FV = U_(), *XFC = U_(), *TMWs = U_();
+  float* TMWs = U_();
   int* TMIs = reinterpret_cast<int*>(U_());
   float *Z = nullptr, *DZ = nullptr, *AZ = nullptr, *XZ = nullptr, *RZ_ = nullptr, *E1Z = nullptr;
   float *E2Z = nullptr, *E3Z = nullptr, *SUBZ = nullptr, *INVZ = nullptr, *CPZ = nullptr, *ALZ = nullptr;
   float *FFZ = nullptr, *GGZ = nullptr;
-  int *ZLO = nullptr, *ZHI = nullptr;
-  float* ZMK = nullptr;
   float *SF0 = nullptr, *SF1 = nullptr, *SX0 = nullptr, *SX1 = nullptr;   // scatter slots
   if (has_z) {
     auto Z_ = [&]() { float* a = p + 2; p += RZ; return a; };
     Z = Z_(); DZ = Z_(); AZ = Z_(); XZ = Z_(); RZ_ = Z_(); E1Z = Z_(); E2Z = Z_(); E3Z = Z_();
-    ZLO = reinterpret_cast<int*>(Z_());
-    ZHI = reinterpret_cast<int*>(Z_());
-    ZMK = Z_();
     SF0 = Z_(); SF1 = Z_(); SX0 = Z_(); SX1 = Z_();
     if (!zjac) {
       SUBZ = Z_(); INVZ = Z_(); CPZ = Z_(); ALZ = Z_(); FFZ = Z_(); GGZ = Z_();
@@ -286,83 +281,106 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       TMIs[i] = mm;
       TMWs[i] = i < n_u ? static_cast<float>(pos - mm * n_t) / static_cast<float>(n_t) : 0.f;
     }
-    // longitudinal row i (node mm = i + 1) gathers from the transverse nodes
-    // [lo, hi] of its hat support (at most four nodes when N_t <= 2 N_l).
-    // Pad rows get an empty range and a zero mask.
-    for (int i = lane; i < kWarp * m_z; i += kWarp) {
-      const int mm = i + 1;
-      int lo = ((mm - 1) * n_t) / n_l + 1;
-      int hi = ((mm + 1) * n_t + n_l - 1) / n_l - 1;
-      lo = lo < 1 ? 1 : lo;
-      hi = hi > n_t - 1 ? n_t - 1 : hi;
-      if (i >= n_z) { lo = 1; hi = 0; }
-      ZLO[i] = lo;
-      ZHI[i] = hi;
-      ZMK[i] = i < n_z ? 1.f : 0.f;
-    }
   }
-  const bool four_slot = n_t <= 2 * n_l;
   __syncwarp();
-  const float inv_nt = 1.f / static_cast<float>(n_t);
   auto interp_z = [&](const float* A, int i) {
     const int mm = TMIs[i];
     const float w = TMWs[i];
     return (1.f - w) * A[mm - 1] + w * A[mm];
   };
-  // (P^T F) at longitudinal row i: hat weights 1 - |l N_l - mm N_t| / N_t
-  // computed from integers, zero outside the support.
-  auto spread4 = [&](const float* F, int i) {
-    const int lo = ZLO[i];
-    const int d0 = lo * n_l - (i + 1) * n_t;
-    float acc = 0.f;
+  // (P^T F) at longitudinal node m = sum over the transverse nodes l of
+  // P[l, m] F_l, P the linear interpolation from the longitudinal to the
+  // transverse nodes.  Transverse node l (row l - 1) lies in the longitudinal
+  // interval [m_l, m_l + 1) and gives (1 - w_l) F_l to node m_l and w_l F_l
+  // to node m_l + 1.  The rows of one interval are consecutive, and each
+  // lane owns consecutive rows, so emit() sums every interval by a segmented
+  // scan (within the lane's rows, then across lanes by shuffles) and the
+  // interval's last row stores the two sums: S0[m] = sum of (1 - w) F over
+  // interval m, S1[m + 1] = sum of w F over it.  Node m then reads
+  // S0[m] + S1[m] (spreadS).  Which slots are written is fixed by the grid,
+  // so the others keep the zeros they were given; pad rows form their own
+  // interval N_l + 1 with weight 0.
+  int mmr[MU];
+  float wr[MU];
+  unsigned lastm = 0;          // bit r: row r is the last row of its interval
+  bool carry_ok = false;       // the lane's first interval began in an earlier lane
+  bool scan_flag = true;       // the lane's last interval begins in this lane
+  int scan_lv = 0;             // shuffle levels that close every interval
+  if (has_z) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int dd = d0 + q * n_l;
-      const float w = fmaxf(0.f, 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt);
-      acc = fmaf(w, F[lo - 1 + q], acc);
-    }
-    return acc;
-  };
-  // wide supports (N_t > 2 N_l): a warp-uniform trip count kz covers every
-  // row's support; weights beyond a row's own support are zero and their
-  // indices stay inside the transverse transfer array (pad rows hold zeros)
-  const int kz = (2 * n_t + n_l - 1) / n_l + 1;
-  auto spreadL = [&](const float* F, int i) {
-    const int lo = ZLO[i];
-    const int d0 = lo * n_l - (i + 1) * n_t;
-    float acc = 0.f;
-    for (int q = 0; q < kz; ++q) {
-      const int dd = d0 + q * n_l;
-      const float w = fmaxf(0.f, 1.f - static_cast<float>(dd < 0 ? -dd : dd) * inv_nt);
-      const int l = lo + q < n_t ? lo + q : n_t - 1;
-      acc = fmaf(w, F[l - 1], acc);
-    }
-    return acc;
-  };
-  // transfer form: 2 = scatter from the transverse nodes (N_l >= N_t: each
-  // transverse node sits in its own longitudinal interval, so node l alone
-  // writes slot S0[m_l] and slot S1[m_l + 1]; the written set is fixed and
-  // every other slot stays zero); 4 = four-slot gather; 0 = wide gather
-  const int zform = n_l >= n_t ? 2 : (four_slot ? 4 : 0);
-  auto emit = [&](const float (&f)[MU], float* G, float* S0, float* S1) {
-    if (zform == 2) {
+    for (int r = 0; r < MU; ++r) { mmr[r] = TMIs[ub + r]; wr[r] = TMWs[ub + r]; }
+    const int nxt = __shfl_down_sync(SFD_FULL, mmr[0], 1);
+    const int prv = __shfl_up_sync(SFD_FULL, mmr[MU - 1], 1);
 #pragma unroll
-      for (int r = 0; r < MU; ++r) {
-        const int mm = TMIs[ub + r];
-        const float w = TMWs[ub + r];
-        S0[mm] = (1.f - w) * f[r];
-        S1[mm + 1] = w * f[r];
+    for (int r = 0; r < MU - 1; ++r)
+      if (mmr[r + 1] != mmr[r]) lastm |= 1u << r;
+    if (lane == kWarp - 1 || nxt != mmr[MU - 1]) lastm |= 1u << (MU - 1);
+#pragma unroll
+    for (int r = 0; r < MU; ++r)
+      if (ub + r >= n_u) lastm &= ~(1u << r);   // pad rows store nothing
+    carry_ok = lane > 0 && prv == mmr[0];
+    scan_flag = !(lane > 0 && prv == mmr[MU - 1]);
+    bool f = scan_flag;
+    for (int l = 0; l < 5 && !__all_sync(SFD_FULL, f); ++l) {
+      const int sh = 1 << l;
+      const bool fu = __shfl_up_sync(SFD_FULL, f ? 1 : 0, sh) != 0;
+      if (lane >= sh) f = f || fu;
+      scan_lv = l + 1;
+    }
+  }
+  // Interval sums of (1 - w) f and w f for NF fields at once (independent
+  // chains interleaved), stored into their slot pairs.
+  auto emit2 = [&](const float (&f)[MU], float* S0, float* S1, const float (&g)[MU], float* T0, float* T1,
+                   bool two) {
+    float a0[MU], a1[MU], b0[MU], b1[MU];
+#pragma unroll
+    for (int r = 0; r < MU; ++r) {
+      const float p0 = (1.f - wr[r]) * f[r], p1 = wr[r] * f[r];
+      const float q0 = (1.f - wr[r]) * g[r], q1 = wr[r] * g[r];
+      const bool cont = r > 0 && mmr[r] == mmr[r > 0 ? r - 1 : 0];
+      a0[r] = cont ? a0[r > 0 ? r - 1 : 0] + p0 : p0;
+      a1[r] = cont ? a1[r > 0 ? r - 1 : 0] + p1 : p1;
+      b0[r] = cont ? b0[r > 0 ? r - 1 : 0] + q0 : q0;
+      b1[r] = cont ? b1[r > 0 ? r - 1 : 0] + q1 : q1;
+    }
+    float v0 = a0[MU - 1], v1 = a1[MU - 1], x0 = b0[MU - 1], x1 = b1[MU - 1];
+    bool fl = scan_flag;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      if (l >= scan_lv) break;
+      const int sh = 1 << l;
+      const float u0 = __shfl_up_sync(SFD_FULL, v0, sh), u1 = __shfl_up_sync(SFD_FULL, v1, sh);
+      float y0 = 0.f, y1 = 0.f;
+      if (two) {
+        y0 = __shfl_up_sync(SFD_FULL, x0, sh);
+        y1 = __shfl_up_sync(SFD_FULL, x1, sh);
       }
-    } else {
+      const bool fu = __shfl_up_sync(SFD_FULL, fl ? 1 : 0, sh) != 0;
+      if (lane >= sh) {
+        if (!fl) { v0 += u0; v1 += u1; x0 += y0; x1 += y1; }
+        fl = fl || fu;
+      }
+    }
+    float c0 = __shfl_up_sync(SFD_FULL, v0, 1), c1 = __shfl_up_sync(SFD_FULL, v1, 1);
+    float d0 = 0.f, d1 = 0.f;
+    if (two) {
+      d0 = __shfl_up_sync(SFD_FULL, x0, 1);
+      d1 = __shfl_up_sync(SFD_FULL, x1, 1);
+    }
 #pragma unroll
-      for (int r = 0; r < MU; ++r) G[ub + r] = f[r];
+    for (int r = 0; r < MU; ++r) {
+      if (!((lastm >> r) & 1u)) continue;
+      const bool add = carry_ok && mmr[r] == mmr[0];
+      S0[mmr[r]] = add ? a0[r] + c0 : a0[r];
+      S1[mmr[r] + 1] = add ? a1[r] + c1 : a1[r];
+      if (two) {
+        T0[mmr[r]] = add ? b0[r] + d0 : b0[r];
+        T1[mmr[r] + 1] = add ? b1[r] + d1 : b1[r];
+      }
     }
   };
+  auto emit = [&](const float (&f)[MU], float* S0, float* S1) { emit2(f, S0, S1, f, S0, S1, false); };
   auto spreadS = [&](const float* S0, const float* S1, int i) { return S0[i + 1] + S1[i + 1]; };
-  auto spread = [&](const float* F, int i) {
-    if (zform == 2) return F == FV ? spreadS(SF0, SF1, i) : spreadS(SX0, SX1, i);
-    return zform == 4 ? spread4(F, i) : spreadL(F, i);
-  };
 
   // ---- constant matrices ----
   Red rdu, rdz;
@@ -524,7 +542,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         }
         RA[r] = i < n_u ? rhs : 0.f;
       }
-      if (has_z) emit(fv, FV, SF0, SF1);
+      if (has_z) emit(fv, SF0, SF1);
       if (!linear) tri_factor_r<MU>(SB, IV, CPr, FFr, GGr, lane, rdu);
       __syncwarp();
 
@@ -542,22 +560,16 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
         // ---- stage 2: longitudinal right-hand side ----
         float dzmax = 0.f;   // lane's largest |Dz|: scale of the longitudinal increments
         {
-          auto rhs_row = [&](int i, auto sp) {
+          auto rhs_row = [&](int i) {
             const float z0 = Z[i], dz0 = DZ[i];
             const float d2z = (Z[i + 1] - z0) - (z0 - Z[i - 1]);
             const float d2dz = (DZ[i + 1] - dz0) - (dz0 - DZ[i - 1]);
             dzmax = fmaxf(dzmax, fabsf(dz0));
-            const float v = lam2l * d2z - 2.f * s0 * dz0 + 2.f * s1l * d2dz + 2.f * cz * sp(FV, i);
+            const float v = lam2l * d2z - 2.f * s0 * dz0 + 2.f * s1l * d2dz + 2.f * cz * spreadS(SF0, SF1, i);
             return i < n_z ? v : 0.f;
           };
           auto st = [&](int i, float v, float) { RZ_[i] = v; };
-          auto sps = [&](const float*, int i) { return spreadS(SF0, SF1, i); };
-          if (zform == 2)
-            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, sps); }, st);
-          else if (zform == 4)
-            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, spread4); }, st);
-          else
-            z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i, spreadL); }, st);
+          z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i); }, st);
         }
         __syncwarp();
         // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
@@ -590,33 +602,34 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
           if (refine) refine_solve(BC, AC);
           // nodal d_+[g d(.)] of the new accelerations for the longitudinal rows
           {
-            float ACe[MU + 2], fc[MU];
+            float ACe[MU + 2], fc[MU], fx[MU];
             extend1<MU>(AC, ACe, lane);
 #pragma unroll
             for (int r = 0; r < MU; ++r)
               fc[r] = GR[r] * (ACe[r + 2] - ACe[r + 1]) - GL[r] * (ACe[r + 1] - ACe[r]);
-            emit(fc, FV, SF0, SF1);
             if (need_resp) {
               float XPe[MU + 2];
               extend1<MU>(XP, XPe, lane);
 #pragma unroll
               for (int r = 0; r < MU; ++r)
-                fc[r] = GR[r] * (XPe[r + 2] - XPe[r + 1]) - GL[r] * (XPe[r + 1] - XPe[r]);
-              emit(fc, XFC, SX0, SX1);
+                fx[r] = GR[r] * (XPe[r + 2] - XPe[r + 1]) - GL[r] * (XPe[r + 1] - XPe[r]);
+              emit2(fc, SF0, SF1, fx, SX0, SX1, true);
+            } else {
+              emit(fc, SF0, SF1);
             }
           }
           __syncwarp();
           float chg = 0.f, mag = 0.f, chx = 0.f, mgx = 0.f;
           if (zjac) {
             // one Jacobi update of each field into the spare buffer, then swap
-            auto jac = [&](int i, float& v, float& x, auto sp, auto spx) {
+            auto jac = [&](int i, float& v, float& x) {
               const bool real = i < n_z;
-              v = (RZ_[i] + cz * sp(FV, i) + s1l * (AZ[i - 1] + AZ[i + 1])) * dz_inv;
+              v = (RZ_[i] + cz * spreadS(SF0, SF1, i) + s1l * (AZ[i - 1] + AZ[i + 1])) * dz_inv;
               v = real ? v : 0.f;
               chg = fmaxf(chg, fabsf(v - AZ[i]));
               mag = fmaxf(mag, fabsf(v));
               if (need_resp) {
-                x = (cz * spx(XFC, i) + s1l * (XZ[i - 1] + XZ[i + 1])) * dz_inv;
+                x = (cz * spreadS(SX0, SX1, i) + s1l * (XZ[i - 1] + XZ[i + 1])) * dz_inv;
                 x = real ? x : 0.f;
                 chx = fmaxf(chx, fabsf(x - XZ[i]));
                 mgx = fmaxf(mgx, fabsf(x));
@@ -626,21 +639,14 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
               E2Z[i] = v;
               if (need_resp) E3Z[i] = x;
             };
-            auto sps = [&](const float*, int i) { return spreadS(SF0, SF1, i); };
-            auto spx = [&](const float*, int i) { return spreadS(SX0, SX1, i); };
-            if (zform == 2)
-              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, sps, spx); }, st);
-            else if (zform == 4)
-              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, spread4, spread4); }, st);
-            else
-              z_rows(m_z, lane, [&](int i, float& v, float& x) { jac(i, v, x, spreadL, spreadL); }, st);
+            z_rows(m_z, lane, jac, st);
             __syncwarp();
             { float* t = AZ; AZ = E2Z; E2Z = t; }
             if (need_resp) { float* t = XZ; XZ = E3Z; E3Z = t; }
           } else {
             for (int r = 0; r < m_z; ++r) {
               const int i = lane * m_z + r;
-              E1Z[i] = i < n_z ? RZ_[i] + cz * spread(FV, i) : 0.f;
+              E1Z[i] = i < n_z ? RZ_[i] + cz * spreadS(SF0, SF1, i) : 0.f;
             }
             tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
             for (int r = 0; r < m_z; ++r) {
@@ -653,7 +659,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
             if (need_resp) {
               for (int r = 0; r < m_z; ++r) {
                 const int i = lane * m_z + r;
-                E1Z[i] = i < n_z ? cz * spread(XFC, i) : 0.f;
+                E1Z[i] = i < n_z ? cz * spreadS(SX0, SX1, i) : 0.f;
               }
               tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
               for (int r = 0; r < m_z; ++r) {

@@ -119,14 +119,14 @@ struct AdjJob {
 };
 
 // Shared-memory words one warp needs for a string with row counts m_u, m_z.
-// Up to kMaxRegRows transverse rows per lane live in registers (4 transverse
+// Up to kMaxRegRows transverse rows per lane live in registers (2 transverse
 // transfer arrays in shared memory); larger grids use the shared-memory path.
 constexpr int kMaxRegRows = 9;
 constexpr int kArraysU = 19;
 constexpr int kArraysZ = 15;
 inline __host__ __device__ int warp_smem_floats(int m_u, int m_z, int z_jacobi) {
   const int ru = kWarp * m_u + 4, rz = m_z > 0 ? kWarp * m_z + 4 : 0;
-  if (m_u <= kMaxRegRows && (m_u & 1)) return 4 * ru + (z_jacobi ? 15 : 21) * rz;
+  if (m_u <= kMaxRegRows && (m_u & 1)) return 2 * ru + (z_jacobi ? 12 : 18) * rz;
   return kArraysU * ru + kArraysZ * rz;
 }
 
