@@ -419,6 +419,11 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
                "sample": f"first {len(sample)} strings of the workload x {args.cpu_samples} samples "
                          f"({dt:.1f} s wall)"}
+        # one thread, for comparison with a single-core figure (a bounded sample)
+        one = strings[:16]
+        r1, _, dt1 = cpu_oracle_rate(one, 24000, threads=1)
+        cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1,
+                                "sample": f"first {len(one)} strings x 24000 samples ({dt1:.1f} s wall)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
