@@ -90,7 +90,7 @@ typedef struct {
   double pickup_pos;      /* output point, fraction of L, default 0.7             */
   double f0_max_ratio;    /* >= 1: grids sized for gamma * ratio (modulation peak) */
   int32_t output;         /* SFD_OUTPUT_*, default transverse; anything else:
-                             SFD_EINVAL.  sfd_tape_create accepts transverse only */
+                             SFD_EINVAL                                            */
   int32_t pad_;
 } sfd_string_params;
 

@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const R bsgn = Dp->boundary == 1 ? -1.0 : 1.0;
   const int en = Dp->e_node, on = Dp->o_node;
   const R ew = Dp->e_w, js = Dp->jscale, ow = Dp->o_w, oscale = Dp->out_scale;
+  const bool zout = Dp->out_ch == 1;   // output reads zeta on the longitudinal grid
+  const int oln = Dp->ol_node;
+  const R olw = Dp->ol_w;
   const R hM = Dp->ham_M, hk2w = Dp->ham_k2w, hexpo = Dp->ham_expo;
 
   // ---- shared memory: FP64 adjoint arrays, then the FP32 trajectory ----
@@ -265,11 +268,30 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       uh = rec[2 * n_u + 2 * n_z]; dh = rec[2 * n_u + 2 * n_z + 1];
     }
   };
-  auto add_output = [&](R dyv) {   // dJ/du of an output sample y = L I(x_o) u
+  // dJ/du of an output sample y = L I(x_o) u, or dJ/dz of y = L I_l(x_o) z
+  // (LD, LDZ also take -c w for the first sample, which reads level 1 - D)
+  auto add_output = [&](R dyv, bool first_level) {
     const R c = dyv * oscale;
-    if (lane == 0) {
-      if (on - 1 >= 0 && on - 1 < n_u) LU[on - 1] += c * (1.0 - ow);
-      if (on >= 0 && on < n_u) LU[on] += c * ow;
+    if (lane != 0) return;
+    if (zout) {
+      if (!has_z) return;   // zeta is identically zero
+      if (oln - 1 >= 0 && oln - 1 < n_z) {
+        LZ[oln - 1] += c * (1.0 - olw);
+        if (first_level) LDZ[oln - 1] -= c * (1.0 - olw);
+      }
+      if (oln >= 0 && oln < n_z) {
+        LZ[oln] += c * olw;
+        if (first_level) LDZ[oln] -= c * olw;
+      }
+    } else {
+      if (on - 1 >= 0 && on - 1 < n_u) {
+        LU[on - 1] += c * (1.0 - ow);
+        if (first_level) LD[on - 1] -= c * (1.0 - ow);
+      }
+      if (on >= 0 && on < n_u) {
+        LU[on] += c * ow;
+        if (first_level) LD[on] -= c * ow;
+      }
     }
   };
 
@@ -286,7 +308,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
 
   for (int64_t m = J.m_end; m > J.m_start; --m) {
     const int64_t n = m - 1;
-    add_output(J.dy[m]);
+    add_output(J.dy[m], false);
     // ---- level n state; a = D(n+1) - D(n) etc. ----
     float uh, dh;
     {
@@ -443,13 +465,9 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
 
   if (J.first) {
     // level 1 output, level 0 output y^0 = L I(u^1 - D^1), initial-state terms
-    add_output(J.dy[1]);
+    add_output(J.dy[1], false);
     __syncwarp();
-    if (lane == 0) {
-      const R c = static_cast<R>(J.dy[0]) * oscale;
-      if (on - 1 >= 0 && on - 1 < n_u) { LU[on - 1] += c * (1.0 - ow); LD[on - 1] -= c * (1.0 - ow); }
-      if (on >= 0 && on < n_u) { LU[on] += c * ow; LD[on] -= c * ow; }
-    }
+    add_output(J.dy[0], true);
     __syncwarp();
     R pa = 0.0;
     if (J.pluck_pos >= 0.f) {   // u^0 = u^1 = c0 tri(x), D^1 = 0

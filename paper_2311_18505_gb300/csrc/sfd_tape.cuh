@@ -88,9 +88,6 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
   for (int i = 0; i < n; ++i)
     if (exc[i].kind != kPluck && exc[i].kind != kHammer)
       return fail(SFD_EINVAL, "string %d: gradients are available for plucked and struck strings", i);
-  for (int i = 0; i < n; ++i)
-    if (params[i].output != SFD_OUTPUT_TRANSVERSE)
-      return fail(SFD_EINVAL, "string %d: gradients are available for the transverse output", i);
   sfd_status rc = set_device(c);
   if (rc) return rc;
   sfd_tape* t = new (std::nothrow) sfd_tape();

@@ -423,7 +423,8 @@ GRAD_PARAM_NAMES = ("kappa", "alpha", "sigma0", "sigma1", "amplitude")
 
 
 def sfd_tape_create(ctx: int, strings, n_samples: int, checkpoint_every: int = 1024) -> int:
-    """Tape of plucked or hammered strings (parameter dicts, no modulation)."""
+    """Tape of plucked or hammered strings (parameter dicts, no modulation; either
+    output channel)."""
     n = len(strings)
     params = (sfd_string_params * n)(*[params_from_dict(d) for d in strings])
     excs = (sfd_excitation * n)(*[excitation_from_dict(d["excitation"]) for d in strings])

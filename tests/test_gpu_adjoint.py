@@ -164,6 +164,58 @@ def test_vector_jacobian_product_matches_the_oracle(sfd, ctx):
         assert np.all(err <= 1e-4 * scale + 2e-3 * np.abs(ref * th)), (i, g[i], ref)
 
 
+def test_vector_jacobian_product_longitudinal_output(sfd, ctx):
+    """The same check for strings read on the longitudinal channel (dJ/dy
+    enters the adjoint of zeta at the pickup).  zeta is forced at sums of
+    transverse partials, so its sensitivity to kappa (which detunes them
+    against the longitudinal modes) follows the FP32 trajectory's small
+    departure from the FP64 one with a large gain: measured, the kappa
+    component is off by 1.8 % where zeta's rel-L2 trajectory error is 7e-5
+    and by < 1e-4 where it is 3e-5 with little detuning.  Each component is
+    held to 1e-4 of the string's largest sensitivity plus max(1 %, 300 x that
+    trajectory error) of itself.  A wrong injection (node, weight, sign,
+    first-sample term) breaks every component by O(1).  (Central differences
+    of the FP32 GPU map are no check here: near a longitudinal mode its
+    kappa-derivative departs from the scheme's by tens of percent, which the
+    adjoint, the derivative of the scheme along the trajectory, does not
+    follow.)"""
+    base, target = workload(8, N_SHORT)
+    base = [dict(d, output="longitudinal") for d in base]
+    target = [dict(d, output="longitudinal") for d in target]
+    tgt = targets_of(target, N_SHORT)
+    tape = sfd.sfd_tape_create(ctx, base, N_SHORT, 1024)
+    try:
+        y = torch.empty(len(base), N_SHORT, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        w = (2.0 * (y.double() - torch.from_numpy(tgt).cuda())).float().contiguous()
+        g = sfd.sfd_tape_backward(tape, w, len(base))
+    finally:
+        sfd.sfd_tape_destroy(tape)
+    w = w.double().cpu().numpy()
+    yg = y.double().cpu().numpy()
+    from paper_2311_18505_gb300.grad import params_of
+    checked = 0
+    for i, d in enumerate(base):
+        nt, nl = oracle.grid(d)
+        if nl <= 1:
+            assert np.all(g[i] == 0.0)   # no longitudinal grid: the output is identically zero
+            continue
+        th = np.array(params_of(d))
+        runs = []
+        for k in range(5):
+            for f in (1 + 1e-6, 1 - 1e-6):
+                runs.append(dict(perturbed(d, k, f), n_t=nt, n_l=nl))
+        ys, _ = oracle.run_batch(runs + [d], n_samples=N_SHORT)
+        ref = np.array([(w[i] @ ys[2 * k] - w[i] @ ys[2 * k + 1]) / (2e-6 * th[k]) for k in range(5)])
+        e_traj = np.linalg.norm(yg[i] - ys[-1]) / np.linalg.norm(ys[-1])
+        scale = np.max(np.abs(ref * th))
+        err = np.abs(g[i] - ref) * th
+        rel = max(1e-2, 300.0 * e_traj)
+        assert np.all(err <= 1e-4 * scale + rel * np.abs(ref * th)), (i, g[i], ref, e_traj)
+        checked += 1
+    assert checked >= 6
+
+
 def oracle_gradient(d, tgt, n, eps=1e-6):
     """Central differences of the FP64 oracle's loss on the string's grid."""
     from paper_2311_18505_gb300.grad import params_of

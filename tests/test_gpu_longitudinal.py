@@ -139,13 +139,9 @@ def test_mixed_channels_in_one_batch(sfd, ctx):
         assert e <= TOL or e <= 3 * fp32_floor(strings[i], strings[i]["n_samples"]), (i, e)
 
 
-def test_invalid_channel_and_tape_refusal(sfd, ctx):
+def test_invalid_channel_is_refused(sfd, ctx):
     p = sfd.params_from_dict(W.make())
     p.output = 2
     with pytest.raises(sfd.SfdError) as ei:
         sfd.sfd_string_create(ctx, p)
-    assert ei.value.code == sfd.SFD_EINVAL
-    d = zeta(alpha=3.0, n_samples=2000)
-    with pytest.raises(sfd.SfdError) as ei:
-        sfd.sfd_tape_create(ctx, [d], 2000, 1024)
     assert ei.value.code == sfd.SFD_EINVAL
