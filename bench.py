@@ -628,13 +628,90 @@ def run_gradient(args, ws, rank, local):
     return 0
 
 
+WORKLOAD_DATASET = ("dataset generation: {count} items x {secs:g} s at 48 kHz drawn per item (seed 0) from the "
+                    "default distribution (f0 log-U[40,1000] Hz, kappa U[0.5,3], alpha U[1,10], pluck/hammer/bow "
+                    "with randomised friction a and eps, 25 % vibrato, 25 % glissando), {shard}-item shards "
+                    "rendered as GPU batches and written to local disk (npz + jsonl)")
+
+
+def run_dataset(args, ws, rank, local):
+    """Time the dataset generator end to end: per-item draws, GPU batch
+    rendering through the C-ABI and shard files on local disk (the writer
+    thread overlaps the next shard's rendering)."""
+    import shutil
+    import tempfile
+    import torch
+    from paper_2311_18505_gb300 import dataset as D
+
+    torch.cuda.set_device(local)
+    count = args.strings or 1024
+    secs = args.seconds or 1.0
+    shard = 256
+    dist = D.Distribution(seconds=secs)
+    render = D.GpuRenderer(local)
+    render_s = [0.0]
+
+    def timed(dicts):
+        t0 = time.perf_counter()
+        out = render(dicts)
+        render_s[0] += time.perf_counter() - t0
+        return out
+
+    root = tempfile.mkdtemp(prefix="sfd_dataset_")
+    try:
+        for w in range(args.warmup):
+            D.generate(os.path.join(root, f"w{w}"), min(count, shard), dist, seed=0, shard_size=shard,
+                       rank=rank, world=ws, render=timed)
+            shutil.rmtree(os.path.join(root, f"w{w}"))
+        barrier(ws)
+        clocks = ClockSampler(local)
+        clocks.start()
+        walls = []
+        render_s[0] = 0.0
+        from paper_2311_18505_gb300 import sfd
+        h2d0, d2h0 = sfd.sfd_ctx_transfer_bytes(render.ctx)
+        for k in range(args.steps):
+            out = os.path.join(root, f"s{k}")
+            t0 = time.perf_counter()
+            D.generate(out, count, dist, seed=0, shard_size=shard, rank=rank, world=ws, render=timed)
+            walls.append(time.perf_counter() - t0)
+            shutil.rmtree(out)
+        clk = clocks.stop()
+        h2d1, d2h1 = sfd.sfd_ctx_transfer_bytes(render.ctx)
+    finally:
+        render.close()
+        shutil.rmtree(root, ignore_errors=True)
+    t_step = max_over_ranks(ws, sum(walls) / len(walls))
+    if rank != 0:
+        return 0
+    n_shards = len(D.shard_ranges(count, shard))
+    mine = len(D.shards_of_rank(n_shards, 0, ws))
+    samples = count * int(round(secs * FS))
+    line = {
+        "metric": METRIC, "value": samples / t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DATASET.format(count=count, secs=secs, shard=shard), "items": count,
+                   "shards": n_shards, "shards_on_rank0": mine,
+                   "timing": "host wall clock around generate() (draws, renders, writes)"},
+        "dataset": {"render_s_per_step": render_s[0] / args.steps, "wall_s_per_step": t_step,
+                    "bytes_written_per_step": samples * 4},
+        "e2e": {"value": samples / t_step, "unit": UNIT, "h2d_bytes_per_step": (h2d1 - h2d0) // args.steps,
+                "d2h_bytes_per_step": (d2h1 - d2h0) // args.steps},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient",
+                                                             "dataset"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: note requests per second")
     ap.add_argument("--trace-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--max-live", type=int, default=8192, help="serving: live-note slots")
@@ -662,6 +739,8 @@ def main(argv=None):
             return run_serving(args, ws, rank, local)
         if args.workload == "gradient":
             return run_gradient(args, ws, rank, local)
+        if args.workload == "dataset":
+            return run_dataset(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1:

@@ -44,6 +44,7 @@ import numpy as np
 from . import workloads as W
 
 FORMAT_VERSION = 1
+GROUP_BYTES = 1 << 30      # output bytes of one rendered group (device pool and host copies)
 
 
 @dataclasses.dataclass
@@ -253,10 +254,16 @@ def _write_shard(out: str, k: int, indices, audio, status, attempts, params, gri
 
 def generate(out: str, count: int, dist: Distribution | None = None, seed: int = 0,
              shard_size: int = 256, rank: int = 0, world: int = 1,
-             render: Renderer | None = None, max_attempts: int = 3, device: int = 0) -> list[int]:
+             render: Renderer | None = None, max_attempts: int = 3, device: int = 0,
+             render_items_max: int = 4096) -> list[int]:
     """Render this rank's shards of a `count`-item dataset into `out`.
-    Rendering of shard k + 1 overlaps the writing of shard k.  Returns the
-    shard numbers written."""
+    Consecutive shards of the rank are rendered together, up to
+    `render_items_max` items per GPU batch (a batch takes about as long as
+    its slowest string, so larger batches keep more of the GPU busy), and
+    the writing of one group overlaps the rendering of the next.  A group
+    also holds at most `GROUP_BYTES` of output (the batch's device output
+    buffer comes from the renderer's pool).  Returns the shard numbers
+    written."""
     dist = dist or Distribution()
     channels(dist)
     os.makedirs(out, exist_ok=True)
@@ -270,7 +277,7 @@ def generate(out: str, count: int, dist: Distribution | None = None, seed: int =
     own = render is None
     if own:
         render = GpuRenderer(device)
-    pending: queue.Queue = queue.Queue(maxsize=1)
+    pending: queue.Queue = queue.Queue(maxsize=max(1, render_items_max // max(shard_size, 1)))
     errors: list[BaseException] = []
 
     def writer():
@@ -285,12 +292,28 @@ def generate(out: str, count: int, dist: Distribution | None = None, seed: int =
 
     th = threading.Thread(target=writer, daemon=True)
     th.start()
+    per_item = len(channels(dist)) * int(round(dist.fs * dist.seconds)) * 4
+    cap = max(1, min(render_items_max, GROUP_BYTES // max(per_item, 1)))
+    groups, cur, size = [], [], 0
+    for k in mine:
+        n = ranges[k][1] - ranges[k][0]
+        if cur and size + n > cap:
+            groups.append(cur)
+            cur, size = [], 0
+        cur.append(k)
+        size += n
+    if cur:
+        groups.append(cur)
     try:
-        for k in mine:
-            a, b = ranges[k]
-            idx = list(range(a, b))
-            res = render_items(render, dist, seed, idx, max_attempts)
-            pending.put((k, idx) + tuple(res))
+        for grp in groups:
+            idx = [i for k in grp for i in range(*ranges[k])]
+            audio, status, attempts, params, grids = render_items(render, dist, seed, idx, max_attempts)
+            o = 0
+            for k in grp:
+                n = ranges[k][1] - ranges[k][0]
+                pending.put((k, idx[o:o + n], audio[o:o + n], status[o:o + n], attempts[o:o + n],
+                             params[o:o + n], grids[o:o + n]))
+                o += n
             if errors:
                 break
     finally:

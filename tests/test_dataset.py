@@ -82,7 +82,7 @@ def test_shard_plan_partitions_the_items():
 def test_generate_writes_shards_and_metadata(tmp_path):
     out = str(tmp_path / "ds")
     render = fake_renderer()
-    written = D.generate(out, 10, SMALL, seed=3, shard_size=4, render=render)
+    written = D.generate(out, 10, SMALL, seed=3, shard_size=4, render=render, render_items_max=4)
     assert written == [0, 1, 2] and render.calls == [4, 4, 2]
     assert D.merge_metadata(out) == 10
     audio, index, status = D.load(out)
@@ -132,12 +132,25 @@ def test_persistent_failure_is_kept_and_flagged(tmp_path):
     assert list(status) == [0, 0, -3, 0]
 
 
+def test_shards_are_rendered_in_groups(tmp_path):
+    render = fake_renderer()
+    D.generate(str(tmp_path / "a"), 10, SMALL, seed=3, shard_size=3, render=render, render_items_max=7)
+    assert render.calls == [6, 4]        # shards {0, 1} then {2, 3}: a group never splits a shard
+    render = fake_renderer()
+    D.generate(str(tmp_path / "b"), 10, SMALL, seed=3, shard_size=3, render=render)
+    assert render.calls == [10]
+    a, _, _ = D.load(str(tmp_path / "a"))
+    b, _, _ = D.load(str(tmp_path / "b"))
+    assert np.array_equal(a, b)
+
+
 def test_dataset_does_not_depend_on_shard_size_or_ranks(tmp_path):
     ref = None
-    for shard, world in ((3, 1), (4, 1), (10, 1), (3, 2), (2, 3)):
-        out = str(tmp_path / f"ds{shard}_{world}")
+    for shard, world, group in ((3, 1, 4096), (4, 1, 4), (10, 1, 1), (3, 2, 6), (2, 3, 4096)):
+        out = str(tmp_path / f"ds{shard}_{world}_{group}")
         for rank in range(world):
-            D.generate(out, 10, SMALL, seed=9, shard_size=shard, rank=rank, world=world, render=fake_renderer())
+            D.generate(out, 10, SMALL, seed=9, shard_size=shard, rank=rank, world=world, render=fake_renderer(),
+                       render_items_max=group)
         D.merge_metadata(out)
         audio, index, _ = D.load(out)
         assert list(index) == list(range(10))
