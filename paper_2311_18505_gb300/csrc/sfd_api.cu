@@ -21,7 +21,7 @@
 namespace sfd {
 #define SFD_DECLARE_LAUNCHER(name)                                                                   \
   cudaError_t name(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta, \
-                   int n_ctas, cudaStream_t stream);
+                   int n_ctas, int pair, cudaStream_t stream);
 SFD_DECLARE_LAUNCHER(launch_synth_reg1)
 SFD_DECLARE_LAUNCHER(launch_synth_reg3)
 SFD_DECLARE_LAUNCHER(launch_synth_reg5)
@@ -137,6 +137,7 @@ struct sfd_ctx {
   Pool pool;
   int sm_count = 0;
   size_t smem_optin = 0;
+  int warp_pairs = 1;                      // 0: every string on one warp (sfd_ctx_set_warp_pairs)
   Job* d_jobs = nullptr;
   int job_cap = 0;
   int* d_counter = nullptr;                // kClasses work-queue counters
@@ -551,7 +552,7 @@ int job_class(const Desc& D) {
   return kClasses - 1;
 }
 
-using Launcher = cudaError_t (*)(const Job*, int, int*, int, int, int, cudaStream_t);
+using Launcher = cudaError_t (*)(const Job*, int, int*, int, int, int, int, cudaStream_t);
 const Launcher kLaunch[kClasses] = {launch_synth_reg1, launch_synth_reg3, launch_synth_reg5,
                                     launch_synth_reg7, launch_synth_reg9, launch_synth_smem};
 
@@ -562,6 +563,7 @@ struct Plan {
   std::vector<Job> jobs;
   int first[kClasses + 1] = {};
   int wf[kClasses] = {};
+  int pair[kClasses] = {};   // 1: the class's strings each get a pair of warps
   int wpc = 1;
 };
 
@@ -605,6 +607,28 @@ sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::
   }
   if (wpc_override >= 1 && wpc_override <= 4) wpc = wpc_override;
   P.wpc = wpc;
+  // Warp pairs: a string stepped by two warps of one SM (both do the
+  // transverse side, each half of the longitudinal rows) finishes its steps
+  // sooner when its longitudinal grid is large.  Classes whose strings have
+  // such grids (m_z >= 3, folded into the sweeps) are paired, heaviest class
+  // first, while the launch's warps stay within one per SM sub-partition, so
+  // pairing only uses schedulers that would otherwise idle.
+  for (int k = 0; k < kClasses; ++k) P.pair[k] = 0;
+  if (c->warp_pairs) {
+    int warps = nj;
+    for (int k = kClasses - 2; k >= 0; --k) {
+      const int n_k = P.first[k + 1] - P.first[k];
+      bool useful = false;
+      for (int i = P.first[k]; i < P.first[k + 1] && !useful; ++i) {
+        const Desc& D = owners[order[i]]->h;
+        useful = D.m_z >= 3 && D.z_jacobi;
+      }
+      if (useful && warps + n_k <= 4 * c->sm_count) {
+        P.pair[k] = 1;
+        warps += n_k;
+      }
+    }
+  }
   return SFD_OK;
 }
 
@@ -623,16 +647,20 @@ sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
     const int n_k = P.first[k + 1] - P.first[k];
     if (n_k == 0) continue;
     const size_t wbytes = static_cast<size_t>(P.wf[k]) * sizeof(float);
-    int wpc = static_cast<int>(std::min<size_t>(static_cast<size_t>(P.wpc), c->smem_optin / wbytes));
-    wpc = std::max(1, wpc);
-    const int n_ctas = (n_k + wpc - 1) / wpc;
+    // strings (regions) per CTA, limited by shared memory; paired: 2 warps each
+    const int per_region = P.pair[k] ? 2 : 1;
+    int regions = static_cast<int>(std::min<size_t>(static_cast<size_t>(P.wpc), c->smem_optin / wbytes));
+    if (P.pair[k]) regions = std::min(regions, 2);
+    regions = std::max(1, regions);
+    const int wpc = regions * per_region;
+    const int n_ctas = (n_k + regions - 1) / regions;
     cudaStream_t st = c->stream;
     if (active > 1) {
       st = c->side[k];
       SFD_CUDA(cudaStreamWaitEvent(st, c->fork, 0));
     }
     if (c->timing) SFD_CUDA(cudaEventRecord(c->t0[k], st));
-    cudaError_t e = kLaunch[k](d_jobs + P.first[k], n_k, c->d_counter + k, P.wf[k], wpc, n_ctas, st);
+    cudaError_t e = kLaunch[k](d_jobs + P.first[k], n_k, c->d_counter + k, P.wf[k], wpc, n_ctas, P.pair[k], st);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     if (c->timing) {
       SFD_CUDA(cudaEventRecord(c->t1[k], st));
@@ -718,7 +746,7 @@ sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes
                 prop.minor);
   }
   c->sm_count = prop.multiProcessorCount;
-  c->smem_optin = prop.sharedMemPerBlockOptin;
+  c->smem_optin = prop.sharedMemPerBlockOptin - kStaticSmemBytes;
   sfd_status rc = c->pool.init(mem_budget_bytes ? mem_budget_bytes : (size_t{256} << 20));
   if (rc) { delete c; return rc; }
   if ((e = cudaMalloc(&c->d_counter, sizeof(int) * kClasses)) != cudaSuccess) {
@@ -769,6 +797,12 @@ int32_t sfd_last_launch_count(const sfd_ctx* c) { return c ? c->last_launches : 
 sfd_status sfd_ctx_set_timing(sfd_ctx* c, int32_t enable) {
   if (!c) return fail(SFD_EINVAL, "ctx is NULL");
   c->timing = enable != 0;
+  return SFD_OK;
+}
+
+sfd_status sfd_ctx_set_warp_pairs(sfd_ctx* c, int32_t enable) {
+  if (!c) return fail(SFD_EINVAL, "ctx is NULL");
+  c->warp_pairs = enable != 0;
   return SFD_OK;
 }
 
@@ -1277,7 +1311,7 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
       e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
       if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
       g_noalloc_ptr[device] = p;
-      g_noalloc_smem[device] = static_cast<size_t>(optin);
+      g_noalloc_smem[device] = static_cast<size_t>(optin) - kStaticSmemBytes;
     }
     base = g_noalloc_ptr[device];
     smem_optin = g_noalloc_smem[device];
@@ -1352,7 +1386,7 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
   const int k = job_class(D);
   int* counter = reinterpret_cast<int*>(b + o_cnt) + k;   // the launcher clears it on `stream`
   e = kLaunch[k](reinterpret_cast<const Job*>(b + o_job), 1, counter,
-                 warp_smem_floats(D.m_u, D.m_z, D.z_jacobi), 1, 1, stream);
+                 warp_smem_floats(D.m_u, D.m_z, D.z_jacobi), 1, 1, 0, stream);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   e = cudaMemcpyAsync(&sc, b + o_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream);
   if (e != cudaSuccess) return cuda_fail(e, "status read");

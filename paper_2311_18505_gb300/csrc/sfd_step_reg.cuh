@@ -184,35 +184,64 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
   }
 }
 
-// Visit the lane's longitudinal rows i = lane + 32 k (k < m_z): full groups
-// of 4 rows compute all four results before any store (so the loads of the
-// group overlap), the remainder row by row.  fn(i, v, x) computes,
-// st(i, v, x) stores.
+// Visit the lane's longitudinal rows i = lane + 32 k for k = k0, k0 + ks, ...
+// < m_z (k0 = 0, ks = 1: all of them; a warp pair splits them by k parity):
+// full groups of 4 rows compute all four results before any store (so the
+// loads of the group overlap), the remainder row by row.  fn(i, v, x)
+// computes, st(i, v, x) stores.
 template <class Fn, class St>
-__device__ __forceinline__ void z_rows(int m_z, int lane, Fn fn, St st) {
-  int k = 0;
-  for (; k + 4 <= m_z; k += 4) {
+__device__ __forceinline__ void z_rows(int m_z, int lane, Fn fn, St st, int k0 = 0, int ks = 1) {
+  int k = k0;
+  for (; k + 3 * ks < m_z; k += 4 * ks) {
     float v[4], x[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) fn(lane + kWarp * (k + q), v[q], x[q]);
+    for (int q = 0; q < 4; ++q) fn(lane + kWarp * (k + q * ks), v[q], x[q]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st(lane + kWarp * (k + q), v[q], x[q]);
+    for (int q = 0; q < 4; ++q) st(lane + kWarp * (k + q * ks), v[q], x[q]);
   }
-  for (; k < m_z; ++k) {
+  for (; k < m_z; k += ks) {
     float v, x;
     fn(lane + kWarp * k, v, x);
     st(lane + kWarp * k, v, x);
   }
 }
 
+// Barrier of the two warps of a pair (named barrier 1 or 2, 64 threads; the
+// ids are immediates so that the kernel reserves only those barriers).
+__device__ __forceinline__ void pair_sync(int id) {
+  if (id == 1)
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 64;" ::: "memory");
+}
+
+// A string may be stepped by one warp (npw = 1) or by a pair of warps of one
+// CTA (npw = 2, pw = 0 or 1, sharing the string's shared-memory region,
+// named barrier bar_id, exchange cells xcell[512]).  Both warps of a pair do
+// the whole transverse side identically (same data, same operations, so the
+// same bits) and split the longitudinal rows by k parity; they meet at a
+// barrier once the state is loaded, once per Gauss-Seidel sweep (where they
+// also take the maximum of each lane's convergence measures, so both see
+// exactly what one warp over all rows would) and once per step after the
+// longitudinal update.  Every barrier sits in control flow that depends
+// only on that shared data.  Only strings with a longitudinal grid folded
+// into the sweeps (z_jacobi) are paired; for any other job the second warp
+// returns at once and the first steps it alone.  Warp 0 of a pair writes
+// the output, the trajectory record and the state.
 template <int MU>
-__device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane) {
+__device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane, int pw = 0, int npw = 1,
+                            int bar_id = 1, float* xcell = nullptr) {
   const Desc* __restrict__ Dp = job.desc;
   const int n_t = Dp->n_t, n_l = Dp->n_l, n_u = Dp->n_u, n_z = Dp->n_z;
   const int m_z = Dp->m_z;
   const bool has_z = m_z > 0;
   const bool linear = Dp->linear != 0;
   const bool zjac = Dp->z_jacobi != 0;
+  const bool paired = npw == 2 && has_z && zjac;
+  if (npw == 2 && !paired && pw != 0) return;   // stepped by the pair's first warp alone
+  const int kz0 = paired ? pw : 0, kzs = paired ? 2 : 1;   // this warp's longitudinal rows
+  const bool writer = !paired || pw == 0;
+  int xpar = 0;                                             // exchange buffer in use
   const int exc = Dp->exc;
   const int RU = kWarp * MU + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
   const float dg = Dp->dg, og = Dp->og, s0 = Dp->s0, s0u = Dp->s0u, s1 = Dp->s1, s1l = Dp->s1l;
@@ -245,8 +274,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     }
   }
   const int total = static_cast<int>(p - wbase);
-  for (int k = lane; k < total; k += kWarp) wbase[k] = 0.f;
+  for (int k = lane + kWarp * kz0; k < total; k += kWarp * kzs) wbase[k] = 0.f;
   __syncwarp();
+  if (paired) pair_sync(bar_id);   // the region is zero before either warp writes to it
 
   // ---- registers: the lane's transverse rows i = lane*MU + r ----
   const int ub = lane * MU;
@@ -257,7 +287,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     U[r] = i < n_u ? Dp->u[i] : 0.f;
     DU[r] = i < n_u ? Dp->du[i] : 0.f;
   }
-  for (int i = lane; i < n_z; i += kWarp) {
+  for (int i = lane + kWarp * kz0; i < n_z; i += kWarp * kzs) {
     Z[i] = Dp->z[i]; DZ[i] = Dp->dz[i]; XZ[i] = Dp->xz[i]; AZ[i] = Dp->az[i];
   }
   Scalars* scp = Dp->sc;
@@ -283,6 +313,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     }
   }
   __syncwarp();
+  if (paired) pair_sync(bar_id);   // both halves of the longitudinal state are loaded
   auto interp_z = [&](const float* A, int i) {
     const int mm = TMIs[i];
     const float w = TMWs[i];
@@ -388,7 +419,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
   const float dz_inv = fast_rcp(dz_diag);
   auto z_axpy = [&](float a) {        // AZ += a XZ over the lane's longitudinal rows
     z_rows(m_z, lane, [&](int i, float& v, float&) { v = fmaf(a, XZ[i], AZ[i]); },
-           [&](int i, float v, float) { AZ[i] = v; });
+           [&](int i, float v, float) { AZ[i] = v; }, kz0, kzs);
   };
   if (has_z && !zjac) {
     for (int r = 0; r < m_z; ++r) {
@@ -569,7 +600,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
             return i < n_z ? v : 0.f;
           };
           auto st = [&](int i, float v, float) { RZ_[i] = v; };
-          z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i); }, st);
+          z_rows(m_z, lane, [&](int i, float& v, float&) { v = rhs_row(i); }, st, kz0, kzs);
         }
         __syncwarp();
         // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
@@ -639,7 +670,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
               E2Z[i] = v;
               if (need_resp) E3Z[i] = x;
             };
-            z_rows(m_z, lane, jac, st);
+            z_rows(m_z, lane, jac, st, kz0, kzs);
             __syncwarp();
             { float* t = AZ; AZ = E2Z; E2Z = t; }
             if (need_resp) { float* t = XZ; XZ = E3Z; E3Z = t; }
@@ -675,6 +706,22 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
           // in this lane and its string-wide scale from the previous step,
           // so one warp reduction per sweep suffices
           mag = fmaxf(mag, dzmax);
+          if (paired) {
+            // each lane's maxima over the pair's rows: the other warp's
+            // updates are in shared memory once both pass the barrier
+            float* xc = xcell + xpar * 256;
+            xc[pw * 128 + lane] = chg;
+            xc[pw * 128 + 32 + lane] = mag;
+            xc[pw * 128 + 64 + lane] = chx;
+            xc[pw * 128 + 96 + lane] = mgx;
+            pair_sync(bar_id);
+            const float* xo = xc + (1 - pw) * 128;
+            chg = fmaxf(chg, xo[lane]);
+            mag = fmaxf(mag, xo[32 + lane]);
+            chx = fmaxf(chx, xo[64 + lane]);
+            mgx = fmaxf(mgx, xo[96 + lane]);
+            xpar ^= 1;
+          }
           float el = chg > 0.f ? chg / fmaxf(mag, scz) : 0.f;
           if (need_resp) el = fmaxf(el, chx > 0.f ? chx / fmaxf(mgx, scx) : 0.f);
           mag_all = fmaxf(mag_all, mag);
@@ -728,12 +775,13 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
       }
       if (has_z) {
         z_rows(m_z, lane, [&](int i, float& d, float& z) { d = DZ[i] + AZ[i]; z = Z[i] + d; },
-               [&](int i, float d, float z) { DZ[i] = d; Z[i] = z; });
+               [&](int i, float d, float z) { DZ[i] = d; Z[i] = z; }, kz0, kzs);
       }
       if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
       __syncwarp();
+      if (paired) pair_sync(bar_id);   // the new level is complete in shared memory
       ++n;
-      if (job.traj) {   // replay for the adjoint: record the new level
+      if (job.traj && writer) {   // replay for the adjoint: record the new level
         float* rec = job.traj + (n - n_first - 1) * job.traj_stride;
 #pragma unroll
         for (int r = 0; r < MU; ++r) {
@@ -760,16 +808,17 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane)
     if (status & kStUnstable) y = 0.f;
     if ((opos & (kWarp - 1)) == lane) outbuf = y;
     ++opos;
-    if ((opos & (kWarp - 1)) == 0) job.out[opos - kWarp + lane] = outbuf;
+    if ((opos & (kWarp - 1)) == 0 && writer) job.out[opos - kWarp + lane] = outbuf;
     ++jnext;
   }
   {
     const int rem = static_cast<int>(opos & (kWarp - 1));
-    if (lane < rem) job.out[opos - rem + lane] = outbuf;
+    if (lane < rem && writer) job.out[opos - rem + lane] = outbuf;
   }
 
   // ---- store the state ----
   __syncwarp();
+  if (!writer) return;
 #pragma unroll
   for (int r = 0; r < MU; ++r) {
     const int i = ub + r;

@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         "sfd_last_launch_count": (i32, [vp]),
         "sfd_ctx_transfer_bytes": (i32, [vp, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "sfd_ctx_set_timing": (i32, [vp, i32]),
+        "sfd_ctx_set_warp_pairs": (i32, [vp, i32]),
         "sfd_ctx_kernel_times": (i32, [vp, P(ctypes.c_float), P(i32)]),
         "sfd_string_kernel_class": (i32, [vp, P(i32)]),
         "sfd_synthesize_noalloc": (i32, [ctypes.c_int, vp, P(sfd_string_params), P(sfd_excitation), i64, vp]),
@@ -333,6 +334,10 @@ SFD_KERNEL_CLASSES = 6
 
 def sfd_ctx_set_timing(ctx: int, enable: bool) -> None:
     _check(lib().sfd_ctx_set_timing(ctx, 1 if enable else 0))
+
+
+def sfd_ctx_set_warp_pairs(ctx: int, enable: bool) -> None:
+    _check(lib().sfd_ctx_set_warp_pairs(ctx, 1 if enable else 0))
 
 
 def sfd_ctx_kernel_times(ctx: int):

@@ -186,3 +186,34 @@ def test_modulated_batch_all_finite(sfd):
     finally:
         torch.cuda.synchronize()
         sfd.sfd_ctx_destroy(ctx)
+
+
+def test_warp_pairs_change_nothing(sfd):
+    """Strings stepped by a pair of warps give the same bits as on one warp:
+    the mixed batch (both channels) and a fine longitudinal grid alone."""
+    ctx = sfd.sfd_ctx_create(0, None, 512 << 20)
+    try:
+        strings = W.batch_mixed(48, seconds=0.05, seed=29)
+        strings += [dict(d, output="longitudinal") for d in strings[:16]]
+        strings.append(W.make(f0=45.0, alpha=1.3, kappa=0.6, excitation={"kind": "hammer", "mass": 6e-3,
+                              "vel": 3.0, "pos": 0.31, "omega": 3000.0, "alpha": 2.5}, n_samples=2400))
+        out = []
+        for pairs in (True, False):
+            sfd.sfd_ctx_set_warp_pairs(ctx, pairs)
+            hs = [sfd.string_from_dict(ctx, d) for d in strings]
+            b = sfd.sfd_batch_create(ctx, hs)
+            ys, st = sfd.sfd_batch_synthesize_host(b, [d["n_samples"] for d in strings], allow_noconv=True)
+            sfd.sfd_batch_destroy(b)
+            states = [sfd.sfd_string_state(h) for h in hs]
+            for h in hs:
+                sfd.sfd_string_destroy(h)
+            out.append((ys, st, states))
+        (ya, sa, za), (yb, sb, zb) = out
+        assert np.array_equal(sa, sb)
+        for a, b in zip(ya, yb):
+            assert np.array_equal(a, b)
+        for a, b in zip(za, zb):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
