@@ -197,16 +197,16 @@ int32_t sfd_last_launch_count(const sfd_ctx* ctx);
 sfd_status sfd_ctx_set_timing(sfd_ctx* ctx, int32_t enable);
 sfd_status sfd_ctx_kernel_times(sfd_ctx* ctx, float* ms, int32_t* n_jobs);
 
-/* Warp pairs (default on).  The time steps of one string are strictly
+/* Warp groups (default on).  The time steps of one string are strictly
  * sequential (the recursion of Eq. 4), so a launch with fewer strings than
  * the GPU has warp schedulers leaves schedulers idle and its time is that of
- * its slowest string.  With pairs enabled, the strings of a kernel class
- * whose longitudinal grid is large (3 or more rows per lane, the
- * longitudinal coupling folded into the Gauss-Seidel sweeps) are each
- * stepped by two warps of one SM, which split the longitudinal rows, as
- * long as the launch then still has at most one warp per scheduler.  The
- * samples are bit for bit the same with and without pairs.  enable = 0
- * steps every string with one warp. */
+ * its slowest string.  With groups enabled, strings whose longitudinal grid
+ * is large (the longitudinal coupling folded into the Gauss-Seidel sweeps;
+ * 3 or more longitudinal rows per lane for 2 warps, 7 or more for 4) are
+ * each stepped by 2 or 4 warps of one SM, which split the longitudinal
+ * rows, as long as the launch then still has at most one warp per
+ * scheduler.  The samples are bit for bit the same with and without groups.
+ * enable = 0 steps every string with one warp. */
 sfd_status sfd_ctx_set_warp_pairs(sfd_ctx* ctx, int32_t enable);
 
 /* Kernel class (0 .. SFD_KERNEL_CLASSES-1) a string runs in. */

@@ -21,7 +21,7 @@
 namespace sfd {
 #define SFD_DECLARE_LAUNCHER(name)                                                                   \
   cudaError_t name(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta, \
-                   int n_ctas, int pair, cudaStream_t stream);
+                   int n_ctas, int group, cudaStream_t stream);
 SFD_DECLARE_LAUNCHER(launch_synth_reg1)
 SFD_DECLARE_LAUNCHER(launch_synth_reg3)
 SFD_DECLARE_LAUNCHER(launch_synth_reg5)
@@ -563,7 +563,7 @@ struct Plan {
   std::vector<Job> jobs;
   int first[kClasses + 1] = {};
   int wf[kClasses] = {};
-  int pair[kClasses] = {};   // 1: the class's strings each get a pair of warps
+  int group[kClasses] = {};  // warps per string of the class's launch (1, 2 or 4)
   int wpc = 1;
 };
 
@@ -607,24 +607,28 @@ sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::
   }
   if (wpc_override >= 1 && wpc_override <= 4) wpc = wpc_override;
   P.wpc = wpc;
-  // Warp pairs: a string stepped by two warps of one SM (both do the
-  // transverse side, each half of the longitudinal rows) finishes its steps
-  // sooner when its longitudinal grid is large.  Classes whose strings have
-  // such grids (m_z >= 3, folded into the sweeps) are paired, heaviest class
-  // first, while the launch's warps stay within one per SM sub-partition, so
-  // pairing only uses schedulers that would otherwise idle.
-  for (int k = 0; k < kClasses; ++k) P.pair[k] = 0;
+  // Warp groups: a string stepped by 2 or 4 warps of one SM (each does the
+  // transverse side, each a share of the longitudinal rows) finishes its
+  // steps sooner when its longitudinal grid is large.  Classes whose strings
+  // have such grids (folded into the sweeps; >= 3 rows per lane for pairs,
+  // >= 7 for groups of 4) get groups, heaviest class first, while the
+  // launch's warps stay within one per SM sub-partition, so groups only use
+  // schedulers that would otherwise idle.
+  for (int k = 0; k < kClasses; ++k) P.group[k] = 1;
   if (c->warp_pairs) {
     int warps = nj;
     for (int k = kClasses - 2; k >= 0; --k) {
       const int n_k = P.first[k + 1] - P.first[k];
-      bool useful = false;
-      for (int i = P.first[k]; i < P.first[k + 1] && !useful; ++i) {
+      int max_mz = 0;
+      for (int i = P.first[k]; i < P.first[k + 1]; ++i) {
         const Desc& D = owners[order[i]]->h;
-        useful = D.m_z >= 3 && D.z_jacobi;
+        if (D.z_jacobi) max_mz = std::max(max_mz, D.m_z);
       }
-      if (useful && warps + n_k <= 4 * c->sm_count) {
-        P.pair[k] = 1;
+      if (max_mz >= 7 && warps + 3 * n_k <= 4 * c->sm_count) {
+        P.group[k] = 4;
+        warps += 3 * n_k;
+      } else if (max_mz >= 3 && warps + n_k <= 4 * c->sm_count) {
+        P.group[k] = 2;
         warps += n_k;
       }
     }
@@ -647,12 +651,12 @@ sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
     const int n_k = P.first[k + 1] - P.first[k];
     if (n_k == 0) continue;
     const size_t wbytes = static_cast<size_t>(P.wf[k]) * sizeof(float);
-    // strings (regions) per CTA, limited by shared memory; paired: 2 warps each
-    const int per_region = P.pair[k] ? 2 : 1;
+    // strings (regions) per CTA, limited by shared memory; a group of warps
+    // per string (at most 4 warps per CTA)
+    const int g = P.group[k];
     int regions = static_cast<int>(std::min<size_t>(static_cast<size_t>(P.wpc), c->smem_optin / wbytes));
-    if (P.pair[k]) regions = std::min(regions, 2);
-    regions = std::max(1, regions);
-    const int wpc = regions * per_region;
+    regions = std::max(1, std::min(regions, 4 / g));
+    const int wpc = regions * g;
     const int n_ctas = (n_k + regions - 1) / regions;
     cudaStream_t st = c->stream;
     if (active > 1) {
@@ -660,7 +664,7 @@ sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
       SFD_CUDA(cudaStreamWaitEvent(st, c->fork, 0));
     }
     if (c->timing) SFD_CUDA(cudaEventRecord(c->t0[k], st));
-    cudaError_t e = kLaunch[k](d_jobs + P.first[k], n_k, c->d_counter + k, P.wf[k], wpc, n_ctas, P.pair[k], st);
+    cudaError_t e = kLaunch[k](d_jobs + P.first[k], n_k, c->d_counter + k, P.wf[k], wpc, n_ctas, P.group[k], st);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     if (c->timing) {
       SFD_CUDA(cudaEventRecord(c->t1[k], st));
@@ -1386,7 +1390,7 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
   const int k = job_class(D);
   int* counter = reinterpret_cast<int*>(b + o_cnt) + k;   // the launcher clears it on `stream`
   e = kLaunch[k](reinterpret_cast<const Job*>(b + o_job), 1, counter,
-                 warp_smem_floats(D.m_u, D.m_z, D.z_jacobi), 1, 1, 0, stream);
+                 warp_smem_floats(D.m_u, D.m_z, D.z_jacobi), 1, 1, 1, stream);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   e = cudaMemcpyAsync(&sc, b + o_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, stream);
   if (e != cudaSuccess) return cuda_fail(e, "status read");

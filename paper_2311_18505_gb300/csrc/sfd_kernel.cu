@@ -50,23 +50,25 @@ namespace sfd {
 // batch, lowers throughput from 124 M to 92 M / 88 M samples/s despite the
 // extra warps.
 //
-// With pair = 1 (register path only) the CTA's warps work in pairs (warps
-// 2p and 2p + 1 share region p and named barrier 1 + p): the pair's first
+// With group = 2 or 4 (register path only) the CTA's warps work in groups
+// (warps g*group .. g*group + group - 1 share region g): the group's first
 // warp takes the next job from the queue and passes it on through shared
-// memory, and both step it (run_job_reg).  The job index cells alternate so
-// that a cell is rewritten only after both warps have passed the next
-// barrier, i.e. after both have read it.
+// memory (named barrier 1 + g over the whole group), and the warps the job
+// can use step it (run_job_reg, in-job barrier 1 + g for pairs, 3 for
+// groups of 4, whose unused warps meanwhile wait at barrier 1).  The job
+// index cells alternate so that a cell is rewritten only after every warp
+// of the group has passed the next barrier, i.e. after all have read it.
 __global__ void __launch_bounds__(128, 1) SFD_KERNEL(const Job* __restrict__ jobs, int n_jobs,
-                                                    int* __restrict__ counter, int warp_floats, int pair) {
+                                                    int* __restrict__ counter, int warp_floats, int group) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & (kWarp - 1);
 #ifdef SFD_MU
-  __shared__ float xcells[2][512];   // per pair: [buffer][warp][chg, mag, chx, mgx][lane]
-  __shared__ int jcell[2][2];        // per pair: job index, alternating
-  const int npw = pair ? 2 : 1;
+  __shared__ float xcells[2][1024];  // per group: [buffer][warp][chg, mag, chx, mgx][lane]
+  __shared__ int jcell[2][2];        // per group: job index, alternating
+  const int npw = group == 4 ? 4 : (group == 2 ? 2 : 1);
 #else
   const int npw = 1;
-  (void)pair;
+  (void)group;
 #endif
   const int pi = warp / npw, pw = warp - pi * npw;
   float* wbase = smem + static_cast<size_t>(pi) * warp_floats;
@@ -78,16 +80,16 @@ __global__ void __launch_bounds__(128, 1) SFD_KERNEL(const Job* __restrict__ job
     if (lane == 0 && pw == 0) j = atomicAdd(counter, 1);
     j = __shfl_sync(SFD_FULL, j, 0);
 #ifdef SFD_MU
-    if (npw == 2) {
+    if (npw > 1) {
       if (pw == 0 && lane == 0) jcell[pi][it & 1] = j;
-      pair_sync(1 + pi);
+      group_sync(1 + pi, npw);
       j = jcell[pi][it & 1];
       ++it;
     }
 #endif
     if (j >= n_jobs) break;
 #ifdef SFD_MU
-    run_job_reg<SFD_MU>(jobs[j], wbase, lane, pw, npw, 1 + pi, npw == 2 ? xcells[pi] : nullptr);
+    run_job_reg<SFD_MU>(jobs[j], wbase, lane, pw, npw, npw == 4 ? 3 : 1 + pi, npw > 1 ? xcells[pi] : nullptr);
 #else
     run_job(jobs[j], wbase, lane);
 #endif
@@ -96,22 +98,24 @@ __global__ void __launch_bounds__(128, 1) SFD_KERNEL(const Job* __restrict__ job
 
 // Host-side launcher of this class (C++ linkage, called by sfd_api.cu).  The
 // job counter is cleared on the same stream before the kernel starts.  With
-// pair = 1 (register classes; warps_per_cta 2 or 4) each string gets a pair
-// of warps and one shared-memory region per pair.
+// group = 2 or 4 (register classes; warps_per_cta a multiple of it, 4 for
+// groups of 4) each string gets a group of warps and one shared-memory
+// region per group.
 cudaError_t SFD_LAUNCHER(const Job* d_jobs, int n_jobs, int* d_counter, int warp_floats, int warps_per_cta,
-                         int n_ctas, int pair, cudaStream_t stream) {
+                         int n_ctas, int group, cudaStream_t stream) {
 #ifndef SFD_MU
-  pair = 0;
+  group = 1;
 #endif
-  if (pair && (warps_per_cta & 1)) return cudaErrorInvalidValue;
-  const int regions = pair ? warps_per_cta / 2 : warps_per_cta;
+  if (group != 1 && group != 2 && group != 4) return cudaErrorInvalidValue;
+  if (warps_per_cta % group != 0 || (group == 4 && warps_per_cta != 4)) return cudaErrorInvalidValue;
+  const int regions = warps_per_cta / group;
   const size_t smem = static_cast<size_t>(warp_floats) * regions * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(SFD_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d_counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  SFD_KERNEL<<<n_ctas, warps_per_cta * kWarp, smem, stream>>>(d_jobs, n_jobs, d_counter, warp_floats, pair);
+  SFD_KERNEL<<<n_ctas, warps_per_cta * kWarp, smem, stream>>>(d_jobs, n_jobs, d_counter, warp_floats, group);
   return cudaGetLastError();
 }
 

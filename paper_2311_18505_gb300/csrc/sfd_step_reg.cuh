@@ -206,28 +206,34 @@ __device__ __forceinline__ void z_rows(int m_z, int lane, Fn fn, St st, int k0 =
   }
 }
 
-// Barrier of the two warps of a pair (named barrier 1 or 2, 64 threads; the
-// ids are immediates so that the kernel reserves only those barriers).
-__device__ __forceinline__ void pair_sync(int id) {
-  if (id == 1)
-    asm volatile("bar.sync 1, 64;" ::: "memory");
-  else
-    asm volatile("bar.sync 2, 64;" ::: "memory");
+// Barrier of the ng warps stepping one string together (named barrier id
+// 1-3, 32 ng threads).  Ids and counts are immediates, so the kernel
+// reserves only those barriers.
+__device__ __forceinline__ void group_sync(int id, int ng) {
+  if (ng == 4) {
+    if (id == 3) asm volatile("bar.sync 3, 128;" ::: "memory");
+    else asm volatile("bar.sync 1, 128;" ::: "memory");
+  } else {
+    if (id == 1) asm volatile("bar.sync 1, 64;" ::: "memory");
+    else if (id == 2) asm volatile("bar.sync 2, 64;" ::: "memory");
+    else asm volatile("bar.sync 3, 64;" ::: "memory");
+  }
 }
 
-// A string may be stepped by one warp (npw = 1) or by a pair of warps of one
-// CTA (npw = 2, pw = 0 or 1, sharing the string's shared-memory region,
-// named barrier bar_id, exchange cells xcell[512]).  Both warps of a pair do
-// the whole transverse side identically (same data, same operations, so the
-// same bits) and split the longitudinal rows by k parity; they meet at a
+// A string may be stepped by one warp or by a group of ng = 2 or 4 warps of
+// one CTA (warp pw of the group; the group launched with npw warps shares
+// the string's shared-memory region, named barrier bar_id and exchange
+// cells xcell[1024]).  Every warp of a group does the whole transverse side
+// identically (same data, same operations, so the same bits), and the
+// group splits the longitudinal rows by k mod ng; the warps meet at a
 // barrier once the state is loaded, once per Gauss-Seidel sweep (where they
-// also take the maximum of each lane's convergence measures, so both see
+// also take the maximum of each lane's convergence measures, so all see
 // exactly what one warp over all rows would) and once per step after the
 // longitudinal update.  Every barrier sits in control flow that depends
-// only on that shared data.  Only strings with a longitudinal grid folded
-// into the sweeps (z_jacobi) are paired; for any other job the second warp
-// returns at once and the first steps it alone.  Warp 0 of a pair writes
-// the output, the trajectory record and the state.
+// only on that shared data.  Only strings whose longitudinal grid is folded
+// into the sweeps (z_jacobi) with at least 3 rows per lane take a group (4
+// warps from 7 rows per lane); the launch's other warps return at once.
+// Warp 0 of a group writes the output, the trajectory record and the state.
 template <int MU>
 __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane, int pw = 0, int npw = 1,
                             int bar_id = 1, float* xcell = nullptr) {
@@ -237,10 +243,13 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   const bool has_z = m_z > 0;
   const bool linear = Dp->linear != 0;
   const bool zjac = Dp->z_jacobi != 0;
-  const bool paired = npw == 2 && has_z && zjac;
-  if (npw == 2 && !paired && pw != 0) return;   // stepped by the pair's first warp alone
-  const int kz0 = paired ? pw : 0, kzs = paired ? 2 : 1;   // this warp's longitudinal rows
-  const bool writer = !paired || pw == 0;
+  int ng = 1;                                  // warps stepping this string
+  if (npw >= 2 && has_z && zjac && m_z >= 3) ng = 2;
+  if (npw == 4 && has_z && zjac && m_z >= 7) ng = 4;
+  if (pw >= ng) return;                       // the group's other warps step it
+  const bool paired = ng > 1;
+  const int kz0 = pw, kzs = ng;               // this warp's longitudinal rows: k = pw, pw + ng, ...
+  const bool writer = pw == 0;
   int xpar = 0;                                             // exchange buffer in use
   const int exc = Dp->exc;
   const int RU = kWarp * MU + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
@@ -276,7 +285,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   const int total = static_cast<int>(p - wbase);
   for (int k = lane + kWarp * kz0; k < total; k += kWarp * kzs) wbase[k] = 0.f;
   __syncwarp();
-  if (paired) pair_sync(bar_id);   // the region is zero before either warp writes to it
+  if (paired) group_sync(bar_id, ng);   // the region is zero before either warp writes to it
 
   // ---- registers: the lane's transverse rows i = lane*MU + r ----
   const int ub = lane * MU;
@@ -313,7 +322,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
     }
   }
   __syncwarp();
-  if (paired) pair_sync(bar_id);   // both halves of the longitudinal state are loaded
+  if (paired) group_sync(bar_id, ng);   // both halves of the longitudinal state are loaded
   auto interp_z = [&](const float* A, int i) {
     const int mm = TMIs[i];
     const float w = TMWs[i];
@@ -707,19 +716,21 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           // so one warp reduction per sweep suffices
           mag = fmaxf(mag, dzmax);
           if (paired) {
-            // each lane's maxima over the pair's rows: the other warp's
-            // updates are in shared memory once both pass the barrier
-            float* xc = xcell + xpar * 256;
+            // each lane's maxima over the group's rows: the other warps'
+            // updates are in shared memory once all pass the barrier
+            float* xc = xcell + xpar * 512;
             xc[pw * 128 + lane] = chg;
             xc[pw * 128 + 32 + lane] = mag;
             xc[pw * 128 + 64 + lane] = chx;
             xc[pw * 128 + 96 + lane] = mgx;
-            pair_sync(bar_id);
-            const float* xo = xc + (1 - pw) * 128;
-            chg = fmaxf(chg, xo[lane]);
-            mag = fmaxf(mag, xo[32 + lane]);
-            chx = fmaxf(chx, xo[64 + lane]);
-            mgx = fmaxf(mgx, xo[96 + lane]);
+            group_sync(bar_id, ng);
+            for (int w = 0; w < ng; ++w) {
+              const float* xo = xc + w * 128;
+              chg = fmaxf(chg, xo[lane]);
+              mag = fmaxf(mag, xo[32 + lane]);
+              chx = fmaxf(chx, xo[64 + lane]);
+              mgx = fmaxf(mgx, xo[96 + lane]);
+            }
             xpar ^= 1;
           }
           float el = chg > 0.f ? chg / fmaxf(mag, scz) : 0.f;
@@ -779,7 +790,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
       }
       if (__any_sync(SFD_FULL, bad)) status |= kStUnstable;
       __syncwarp();
-      if (paired) pair_sync(bar_id);   // the new level is complete in shared memory
+      if (paired) group_sync(bar_id, ng);   // the new level is complete in shared memory
       ++n;
       if (job.traj && writer) {   // replay for the adjoint: record the new level
         float* rec = job.traj + (n - n_first - 1) * job.traj_stride;

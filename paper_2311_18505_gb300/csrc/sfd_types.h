@@ -124,7 +124,7 @@ struct AdjJob {
 constexpr int kMaxRegRows = 9;
 // static shared memory of the register-path kernels (the warp pairs'
 // exchange cells and job index cells); dynamic regions get the rest
-constexpr int kStaticSmemBytes = 2 * 512 * 4 + 4 * 4;
+constexpr int kStaticSmemBytes = 2 * 1024 * 4 + 4 * 4;
 constexpr int kArraysU = 19;
 constexpr int kArraysZ = 15;
 inline __host__ __device__ int warp_smem_floats(int m_u, int m_z, int z_jacobi) {
