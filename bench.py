@@ -270,6 +270,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(dev)            # the context's stream (also the capture stream)
     torch.cuda.set_stream(stream)
     ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 4 << 30)
+    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
     strings, workload_name = make_workload(args, rank)
     graphed = args.workload == "modulated"
     ns = np.array([d["n_samples"] for d in strings], dtype=np.int64)
@@ -480,6 +481,7 @@ def run_serving(args, ws, rank, local):
     secs = args.trace_seconds
     trace = W.serving_trace(args.rate, secs, seed=5 + 1000 * rank)
     ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 2 << 30)
+    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
     sv = sfd.sfd_server_create(ctx, 1024, args.max_live)
     reqs = [sfd.request_from_dict(d, i) for i, (_, d) in enumerate(trace)]   # marshalled before the clock starts
 
@@ -572,6 +574,7 @@ def run_gradient(args, ws, rank, local):
     base, target = W.batch_gradient(64, seconds=0.5, seed=4 + 1000 * rank)
     n = base[0]["n_samples"]
     ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 1 << 30)
+    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
     # targets rendered by the same synthesis
     hs = [sfd.string_from_dict(ctx, d) for d in target]
     b = sfd.sfd_batch_create(ctx, hs)
@@ -649,6 +652,8 @@ def run_dataset(args, ws, rank, local):
     shard = 256
     dist = D.Distribution(seconds=secs)
     render = D.GpuRenderer(local)
+    from paper_2311_18505_gb300 import sfd as _sfd
+    _sfd.sfd_ctx_set_warp_pairs(render.ctx, bool(args.warp_groups))
     render_s = [0.0]
 
     def timed(dicts):
@@ -718,6 +723,8 @@ def parse_args(argv=None):
     ap.add_argument("--strings", type=int, default=0)
     ap.add_argument("--seconds", type=float, default=0.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--warp-groups", type=int, default=1, choices=[0, 1],
+                    help="1: large-grid strings may take 2 or 4 warps (sfd_ctx_set_warp_pairs)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # oracle samples: the whole 256 x 2 s batch for the baseline (~17 s on 16
