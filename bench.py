@@ -709,6 +709,74 @@ def run_dataset(args, ws, rank, local):
     return 0
 
 
+WORKLOAD_SINGLE = ("single string (config 1): f0 110 Hz, kappa 1, alpha {alpha:g}, sigma0 0.5, sigma1 1e-5, 1 mm "
+                   "pluck at 0.3, pickup 0.7, 1 s at 48 kHz, one sfd_synthesize call per step")
+
+
+def run_single(args, ws, rank, local):
+    """Plain single-string stepping: one string per launch (one warp, or a
+    warp group when its longitudinal grid is large), the form the batched,
+    served and graph-replayed launches are compared with."""
+    import torch
+    from paper_2311_18505_gb300 import build as B
+    B.build()
+    from paper_2311_18505_gb300 import sfd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 256 << 20)
+    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
+    alpha = args.alpha
+    d = W.single_string(alpha=alpha, seconds=args.seconds or 1.0)
+    n = d["n_samples"]
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    ms = []
+    clocks = ClockSampler(local)
+    for k in range(args.warmup + args.steps):
+        h = sfd.string_from_dict(ctx, d)
+        if k == args.warmup:
+            barrier(ws)
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        sfd.sfd_synthesize(h, n, out)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+        sfd.sfd_string_destroy(h)
+    clk = clocks.stop()
+    nt, nl = string_grid(d, sfd, ctx)
+    sfd.sfd_ctx_destroy(ctx)
+    t = max_over_ranks(ws, sum(ms) / len(ms) / 1e3)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": ws * n / t, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SINGLE.format(alpha=alpha), "strings": 1, "n_t": nt, "n_l": nl,
+                   "timing": "CUDA events around sfd_synthesize on the context stream (device output)"},
+        "grid_point_updates_per_s": (nt - 1 + (nl - 1 if alpha > 1 else 0)) * (n - 2) / t,
+        "realtime_factor": (n / FS) / t,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def string_grid(d, sfd, ctx):
+    """(N_t, N_l) of a string as the library sizes it."""
+    h = sfd.string_from_dict(ctx, d)
+    try:
+        return tuple(sfd.sfd_string_info(h)[:2])
+    finally:
+        sfd.sfd_string_destroy(h)
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,7 +784,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient",
-                                                             "dataset"])
+                                                             "dataset", "single"])
+    ap.add_argument("--alpha", type=float, default=1.0, help="single: stiffness-to-tension ratio (1 or 3)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: note requests per second")
     ap.add_argument("--trace-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--max-live", type=int, default=8192, help="serving: live-note slots")
@@ -748,6 +817,8 @@ def main(argv=None):
             return run_gradient(args, ws, rank, local)
         if args.workload == "dataset":
             return run_dataset(args, ws, rank, local)
+        if args.workload == "single":
+            return run_single(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1:
