@@ -352,16 +352,20 @@ sfd_status sfd_server_destroy(sfd_server* sv);
  * Gradients of a waveform loss with respect to string parameters, by the
  * discrete adjoint of the time-stepping (no counterpart in the paper).
  *
- * A tape holds n strings (params[i], exc[i]: pluck or hammer, no f0
+ * A tape holds n strings (params[i], exc[i]: pluck, hammer or bow, no f0
  * modulation) synthesized for n_samples each.  sfd_tape_forward writes the
  * audio y (device, y[i * n_samples + j], metres) and keeps every string's
  * state every checkpoint_every samples.  sfd_tape_backward takes dJ/dy
  * (device, same layout) and writes, per string, dJ/d(kappa, alpha, sigma0,
  * sigma1, amplitude) to grad[i * SFD_GRAD_PARAMS + k] (host): amplitude is
- * the pluck amp_m, or the hammer vel_mps.  The gradient is that of the
- * discrete scheme on the string's grid (N_t, N_l held fixed), through the
- * FP32 trajectory the forward computed: each segment between checkpoints is
- * replayed from its checkpoint and swept backwards by the adjoint kernel.
+ * the pluck amp_m, the hammer vel_mps, or the bow velocity vel_mps.  The
+ * gradient is that of the discrete scheme on the string's grid (N_t, N_l
+ * held fixed), through the FP32 trajectory the forward computed: each
+ * segment between checkpoints is replayed from its checkpoint and swept
+ * backwards by the adjoint kernel.  For a bowed string each step keeps the
+ * regime (sliding or sticking, Sec. 3.3.1) the forward took: the loss is
+ * piecewise smooth in the parameters, and this is its derivative between
+ * regime switches.
  * The tape's own device memory (checkpoints, one segment's replay record,
  * adjoint state) is allocated at create; the strings come from the ctx pool.
  * --------------------------------------------------------------------- */

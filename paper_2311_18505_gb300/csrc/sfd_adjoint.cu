@@ -85,6 +85,9 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const int oln = Dp->ol_node;
   const R olw = Dp->ol_w;
   const R hM = Dp->ham_M, hk2w = Dp->ham_k2w, hexpo = Dp->ham_expo;
+  const bool bow = Dp->exc == kBow;
+  const R bF = Dp->bow_F, ba = Dp->bow_a, beps = Dp->bow_eps, kk = Dp->k;
+  const int64_t brel = Dp->bow_release_n;
 
   // ---- shared memory: FP64 adjoint arrays, then the FP32 trajectory ----
   double* pd = smem_d;
@@ -295,12 +298,12 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     }
   };
 
-  // D at level m_end (the first step's "next" level)
-  float dh1;
+  // D at level m_end (the first step's "next" level); for a bowed string the
+  // level's u_H slot holds the bow velocity of the step that produced it
+  float uh1, dh1;
   {
     const float *pu, *pdu, *pz, *pdz;
-    float uh;
-    level_ptr(J.m_end, pu, pdu, pz, pdz, uh, dh1);
+    level_ptr(J.m_end, pu, pdu, pz, pdz, uh1, dh1);
     for (int i = lane; i < n_u; i += kWarp) DN1[i] = pdu[i];
     for (int i = lane; i < n_z; i += kWarp) DZN1[i] = pdz[i];
   }
@@ -357,6 +360,13 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     __syncwarp();
     coupled(RA, RZ_, NA, NZ);
     R nus = mus;
+    // bow (Eq. 5) with force on: sliding, R3 = s + k^2 F phi(v) with
+    // v = I(a + 2D) / 2k - v_B; sticking (v = 0), R3 = v.  Either way M^T
+    // adds a rank-one term along the unit-force response.
+    const bool bow_on = bow && n < brel && bF > 0.0;
+    const R vb = uh1;
+    R phid = 0.0;
+    if (bow_on) phid = -ba * (1.0 - beps) * exp(-ba * fabs(vb));
     if (hammer && k2G > 0.0) {
       const R rs = -(hM * k2G / (2.0 * js)) * mus;
       for (int r = 0; r < m_u; ++r) {
@@ -374,6 +384,29 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
       for (int i = lane; i < n_z; i += kWarp) NZ[i] = fma(st, XZ[i], NZ[i]);
       nus = -(2.0 * js / (hM * k2G)) * st;
+      __syncwarp();
+    } else if (bow_on) {
+      for (int r = 0; r < m_u; ++r) {
+        const int i = ub + r;
+        R v = 0.0;
+        if (i == en - 1) v += (1.0 - ew) * js;
+        if (i == en) v += ew * js;
+        T1[i] = i < n_u ? v : 0.0;
+      }
+      __syncwarp();
+      coupled(T1, nullptr, XP, XZ);
+      const R ia = (1.0 - ew) * NA[en - 1] + ew * NA[en], ix = (1.0 - ew) * XP[en - 1] + ew * XP[en];
+      R st;
+      if (vb == 0.0) {   // sticking: I nu_a = 0
+        st = -ia / ix;
+        nus = 2.0 * kk * js * st;
+      } else {           // sliding
+        const R bj = 0.5 * kk * bF * phid;
+        st = -bj * ia / (1.0 + bj * ix);
+        nus = -js * (ia + st * ix);
+      }
+      for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
+      for (int i = lane; i < n_z; i += kWarp) NZ[i] = fma(st, XZ[i], NZ[i]);
       __syncwarp();
     }
     // nu_z = (cb / cz) nz; the warm start of the next step keeps nz
@@ -453,6 +486,13 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       ldh = ldh + luh;
       luh = luh + psi_eta;
     }
+    if (bow_on && lane == 0) {
+      // (dR3/dD)^T nu_s and dR3/dv_B (the amplitude slot of a bowed string)
+      const R cd = vb == 0.0 ? 1.0 / kk : kk * bF * phid;
+      if (en - 1 >= 0 && en - 1 < n_u) LD[en - 1] += cd * (1.0 - ew) * nus;
+      if (en >= 0 && en < n_u) LD[en] += cd * ew * nus;
+      pg[kGAmp] += vb == 0.0 ? -nus : -kk * kk * bF * phid * nus;
+    }
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < kGradSlots; ++k) acc[k] += pg[k];
@@ -460,6 +500,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     { float* t = DN1; DN1 = DU; DU = t; }
     if (has_z) { float* t = DZN1; DZN1 = DZ; DZ = t; }
     dh1 = dh;
+    uh1 = uh;
     __syncwarp();
   }
 

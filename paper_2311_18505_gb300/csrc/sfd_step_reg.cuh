@@ -525,6 +525,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
       const float ca = ca_0 * rm, cb = cb_0 * rm, cz = cz_0 * rm;
 
       float eta = 0.f, k2G = 0.f, FB = 0.f;
+      float vrec = 0.f;   // bow: relative velocity of the step (0 while sticking), for the adjoint
       if (exc == kHammer) {
         eta = uh - node_interp<MU>(U, en, ew, n_u);
         if (eta > 0.f) k2G = ham_k2w * powf(eta, ham_expo);
@@ -770,6 +771,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
                         bow_v;
         const float c = 0.5f * kk * FB * node_interp<MU>(XP, en, ew, n_u);
         const float phi = bow_phi(b, c, bow_a, bow_eps, bow_w);
+        vrec = !(c > 0.f) ? b : (fabsf(b) <= c ? 0.f : b - c * phi);
         const float s = -k2 * FB * phi;
 #pragma unroll
         for (int r = 0; r < MU; ++r) AC[r] = fmaf(s, XP[r], AC[r]);
@@ -800,7 +802,8 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           if (i < n_u) { rec[i] = U[r]; rec[n_u + i] = DU[r]; }
         }
         for (int i = lane; i < n_z; i += kWarp) { rec[2 * n_u + i] = Z[i]; rec[2 * n_u + n_z + i] = DZ[i]; }
-        if (lane == 0) { rec[2 * n_u + 2 * n_z] = uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
+        // (a bowed string has no hammer state: its slot holds the step's bow velocity)
+        if (lane == 0) { rec[2 * n_u + 2 * n_z] = exc == kBow ? vrec : uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
       }
     }
     float y;

@@ -216,6 +216,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
 
       // excitation scalars at time level n
       float eta = 0.f, k2G = 0.f, FB = 0.f;
+      float vrec = 0.f;   // bow: relative velocity of the step (0 while sticking), for the adjoint
       if (exc == kHammer) {
         eta = uh - interp2(U, en, ew);
         if (eta > 0.f) k2G = Dp->ham_k2w * powf(eta, Dp->ham_expo);
@@ -381,6 +382,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) / (2.f * k) - Dp->bow_v;
         const float c = 0.5f * k * FB * interp2(XP, en, ew);
         const float phi = bow_phi(b, c, Dp->bow_a, Dp->bow_eps, bow_w);
+        vrec = !(c > 0.f) ? b : (fabsf(b) <= c ? 0.f : b - c * phi);
         const float s = -Dp->k2 * FB * phi;
         for (int r = 0; r < m_u; ++r) AC[ub + r] = fmaf(s, XP[ub + r], AC[ub + r]);
         if (has_z)
@@ -416,7 +418,8 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         float* rec = job.traj + (n - n_first - 1) * job.traj_stride;
         for (int i = lane; i < n_u; i += kWarp) { rec[i] = U[i]; rec[n_u + i] = DU[i]; }
         for (int i = lane; i < n_z; i += kWarp) { rec[2 * n_u + i] = Z[i]; rec[2 * n_u + n_z + i] = DZ[i]; }
-        if (lane == 0) { rec[2 * n_u + 2 * n_z] = uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
+        // (a bowed string has no hammer state: its slot holds the step's bow velocity)
+        if (lane == 0) { rec[2 * n_u + 2 * n_z] = exc == kBow ? vrec : uh; rec[2 * n_u + 2 * n_z + 1] = duh; }
       }
     }
     // output sample j = jnext: u^n or u^{n-1}, or zeta (zeros once unstable)

@@ -86,8 +86,8 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
   if (n <= 0 || n_samples < 2 || checkpoint_every < 2)
     return fail(SFD_EINVAL, "need n > 0 strings, n_samples >= 2 and checkpoint_every >= 2");
   for (int i = 0; i < n; ++i)
-    if (exc[i].kind != kPluck && exc[i].kind != kHammer)
-      return fail(SFD_EINVAL, "string %d: gradients are available for plucked and struck strings", i);
+    if (exc[i].kind != kPluck && exc[i].kind != kHammer && exc[i].kind != kBow)
+      return fail(SFD_EINVAL, "string %d: unknown excitation", i);
   sfd_status rc = set_device(c);
   if (rc) return rc;
   sfd_tape* t = new (std::nothrow) sfd_tape();
@@ -103,8 +103,9 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
     if (rc) break;
     t->fw.push_back(s);
     const sfd_excitation& e = exc[i];
-    rc = e.kind == kPluck ? sfd_excite_pluck(s, e.amp_m, e.pos)
-                          : sfd_excite_hammer(s, e.mass_kg, e.vel_mps, e.pos, e.omega_h, e.alpha_h);
+    rc = e.kind == kPluck    ? sfd_excite_pluck(s, e.amp_m, e.pos)
+         : e.kind == kHammer ? sfd_excite_hammer(s, e.mass_kg, e.vel_mps, e.pos, e.omega_h, e.alpha_h)
+                             : sfd_excite_bow(s, e.vel_mps, e.force_n, e.pos, e.a_s_per_m, e.eps, e.release_time_s);
     if (rc) break;
     sfd_string* r = nullptr;
     rc = clone_string(s, &r);

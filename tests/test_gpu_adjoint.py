@@ -216,6 +216,60 @@ def test_vector_jacobian_product_longitudinal_output(sfd, ctx):
     assert checked >= 6
 
 
+def _bow(vel, force, pos=0.21, a=100.0, eps=0.1):
+    return {"kind": "bow", "vel": vel, "force": force, "pos": pos, "a": a, "eps": eps, "release": -1.0}
+
+
+def test_bowed_strings_vector_jacobian_product(sfd, ctx):
+    """Bowed strings (Eq. 5): each step keeps the regime the forward took
+    (sliding: the force follows the friction curve; sticking: the bow point
+    moves with the bow), so the loss is piecewise smooth and the adjoint
+    gives its derivative between switches.  Against central differences of
+    the FP64 oracle (relative steps 1e-6 and 1e-5, grid fixed), on the
+    components where the two quotients agree to 1 % (elsewhere a switch
+    falls inside the step or the sensitivity is at rounding level): each
+    within 1e-4 of the string's largest sensitivity plus 3 % of itself
+    (measured up to 1.7 %, on kappa of a string that sticks and slips).  The
+    cases: sliding bows, a stick-slip bow and the longitudinal channel."""
+    n = N_SHORT
+    cases = [W.make(f0=220.0, alpha=2.0, excitation=_bow(0.4, 0.1), n_samples=n),
+             W.make(f0=150.0, alpha=3.0, kappa=1.5, excitation=_bow(0.3, 0.2), n_samples=n),
+             W.make(f0=196.0, alpha=2.5, excitation=_bow(0.2, 1.0), n_samples=n),
+             dict(W.make(f0=220.0, alpha=2.0, excitation=_bow(0.4, 0.1), n_samples=n), output="longitudinal")]
+    from paper_2311_18505_gb300.grad import params_of, with_params
+    rng = np.random.default_rng(8)
+    checked = 0
+    for d in cases:
+        r0 = np.array(params_of(d)) * (1 + rng.uniform(-0.05, 0.05, 5))
+        r0[1] = max(r0[1], 1.0)
+        tgt = oracle.run(with_params(d, r0), n)
+        tape = sfd.sfd_tape_create(ctx, [d], n, 1024)
+        try:
+            y = torch.empty(1, n, device="cuda", dtype=torch.float32)
+            sfd.sfd_tape_forward(tape, y)
+            w = (2.0 * (y.double() - torch.from_numpy(tgt).cuda())).float().contiguous()
+            g = sfd.sfd_tape_backward(tape, w, 1)[0]
+        finally:
+            sfd.sfd_tape_destroy(tape)
+        w = w.double().cpu().numpy()[0]
+        nt, nl = oracle.grid(d)
+        th = np.array(params_of(d))
+        quot = []
+        for eps in (1e-6, 1e-5):
+            runs = [dict(perturbed(d, k, f), n_t=nt, n_l=nl) for k in range(5) for f in (1 + eps, 1 - eps)]
+            ys, _ = oracle.run_batch(runs, n_samples=n)
+            quot.append(np.array([(w @ ys[2 * k] - w @ ys[2 * k + 1]) / (2 * eps * th[k]) for k in range(5)]))
+        ref = quot[0]
+        scale = np.max(np.abs(ref * th))
+        for k in range(5):
+            if ref[k] == 0.0 or abs(quot[0][k] - quot[1][k]) > 1e-2 * abs(ref[k]):
+                continue
+            err = abs(g[k] - ref[k]) * th[k]
+            assert err <= 1e-4 * scale + 3e-2 * abs(ref[k] * th[k]), (d["f0"], k, g[k], ref[k])
+            checked += 1
+    assert checked >= 12
+
+
 def oracle_gradient(d, tgt, n, eps=1e-6):
     """Central differences of the FP64 oracle's loss on the string's grid."""
     from paper_2311_18505_gb300.grad import params_of
