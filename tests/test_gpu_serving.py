@@ -180,3 +180,24 @@ def test_unstable_note_is_isolated(sfd):
     finally:
         sfd.sfd_server_destroy(sv)
         sfd.sfd_ctx_destroy(ctx)
+
+
+def test_longitudinal_notes_served(sfd):
+    """Notes read on the longitudinal channel, served beside transverse ones,
+    equal the same notes alone."""
+    ctx = sfd.sfd_ctx_create(0, None, 128 << 20)
+    sv = sfd.sfd_server_create(ctx, CHUNK, 32)
+    try:
+        notes = short_notes(0.004, seed=17, lo=1500, hi=4000)[:8]
+        notes = [dict(d, output="longitudinal") if i % 2 else d for i, d in enumerate(notes)]
+        for tag, d in enumerate(notes):
+            sfd.sfd_server_submit(sv, sfd.request_from_dict(d, tag))
+        audio, stats_log, finished = {}, [], {}
+        drain(sfd, sv, audio, stats_log, finished)
+        assert sorted(finished) == list(range(len(notes)))
+        for tag, d in enumerate(notes):
+            assert finished[tag] == sfd.SFD_OK
+            assert np.array_equal(np.concatenate(audio[tag]), alone(sfd, ctx, d)), tag
+    finally:
+        sfd.sfd_server_destroy(sv)
+        sfd.sfd_ctx_destroy(ctx)
