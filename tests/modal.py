@@ -75,3 +75,33 @@ def fletcher_clamped(f0: float, K: float, p: int) -> float:
 def simply_supported(f0: float, K: float, n: int) -> float:
     """Continuum simply-supported stiff string: f_n = n f0 sqrt(1 + K n^2)."""
     return n * f0 * math.sqrt(1 + K * n * n)
+
+
+def modulated_solution(n_t: int, d: dict, gammas: np.ndarray, u0: np.ndarray, u1: np.ndarray,
+                       n_samples: int, x_o: float) -> np.ndarray:
+    """y^j of the linear simply-supported scheme when the wave speed of the
+    step n -> n+1 is gammas[n]: each sine mode follows the same two-term
+    recurrence with Om2 built from gammas[n], stepped in time."""
+    h, k = 1.0 / n_t, 1.0 / d["fs"]
+    L = d.get("length", 1.0)
+    p = np.arange(1, n_t)
+    s = np.sin(p * math.pi * h / 2.0) ** 2
+    th = 1.0 - 2.0 * (1.0 - d["theta"]) * s
+    stiff = 16 * d["kappa"] ** 2 * k ** 2 * s ** 2 / h ** 4
+    sig = d["sigma0"] * k + 4 * d["sigma1"] * k * s / h ** 2
+    l = np.arange(1, n_t)
+    Sm = np.sin(np.outer(p, l) * math.pi * h)
+    a_prev, a = (2.0 / n_t) * Sm @ u0, (2.0 / n_t) * Sm @ u1
+    Io = np.maximum(0.0, 1.0 - np.abs(l * h - x_o) / h)
+    Ip = Io @ Sm.T
+    y = np.zeros(n_samples)
+    if n_samples > 0:
+        y[0] = L * a_prev @ Ip
+    if n_samples > 1:
+        y[1] = L * a @ Ip
+    for n in range(1, n_samples - 1):
+        om2 = 4 * gammas[n] ** 2 * k ** 2 * s / h ** 2 + stiff
+        a_next = ((2 * th - om2) * a - (th - sig) * a_prev) / (th + sig)
+        a_prev, a = a, a_next
+        y[n + 1] = L * a @ Ip
+    return y

@@ -13,7 +13,7 @@ import oracle
 from paper_2311_18505_gb300 import workloads as W
 from brute_matrix import Brute
 from fdtd_energy import Grid, dissipation, energy
-from modal import discrete_frequency, dst_solution, fletcher_clamped, simply_supported
+from modal import discrete_frequency, dst_solution, fletcher_clamped, modulated_solution, simply_supported
 from pitch import peak_frequency
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
@@ -122,6 +122,56 @@ def test_dst_modal_solution(sigma0, sigma1, kappa):
     y = s.run(12000)
     ym = dst_solution(s.n_t, d, up, u, 12000, d["pickup"])
     assert np.max(np.abs(y - ym)) <= 1e-10 * np.max(np.abs(ym))
+
+
+# ---------------------------------------------------------- f0 modulation
+
+def _wave_speeds(d, n):
+    """gamma^n of the step n -> n+1 (reading A14): vibrato
+    gamma 2^{(c/1200) sin(2 pi f_v n k + phi)}, glissando gamma 2^{D n k / T}."""
+    g, t = 2.0 * d["f0"], np.arange(n) / d["fs"]
+    m = d["modulation"]
+    if m["kind"] == "vibrato":
+        return g * 2.0 ** (m["depth"] / 1200.0 * np.sin(2 * math.pi * m["rate"] * t + m["phase"]))
+    if m["kind"] == "gliss":
+        return g * 2.0 ** (m["depth"] * t / m["duration"])
+    return np.full(n, g)
+
+
+@pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 6.0, "depth": 40.0, "phase": 0.7},
+                                 {"kind": "gliss", "depth": 1.0, "duration": 0.25},
+                                 {"kind": "gliss", "depth": -0.5, "duration": 0.25}])
+def test_modulated_modal_recursion(mod):
+    """A linear simply-supported string with a modulated wave speed: each sine
+    mode's recurrence, stepped with the step's gamma^n, gives the oracle's
+    output to 1e-9 (on the grid sized for the peak gamma)."""
+    d = W.make(boundary=1, sigma0=0.3, sigma1=2e-5, kappa=1.5, modulation=mod)
+    s = oracle.OracleString(d)
+    up, u, *_ = s.state()
+    n = 12000
+    y = s.run(n)
+    ym = modulated_solution(s.n_t, d, _wave_speeds(d, n), up, u, n, d["pickup"])
+    assert np.max(np.abs(y - ym)) <= 1e-9 * np.max(np.abs(ym))
+
+
+def test_glissando_pitch_rises_an_octave():
+    """An octave glissando over 1 s: the fundamental measured near the end is
+    2^0.8 times the one measured near the start (window centres 0.1 s and
+    0.9 s), within 0.5 %."""
+    d = W.make(kappa=0.1, sigma0=0.2, sigma1=1e-6, modulation={"kind": "gliss", "depth": 1.0, "duration": 1.0},
+               excitation={"kind": "pluck", "amp": 1e-3, "pos": 0.3}, n_samples=48000)
+    y = oracle.run(d)
+    f_a = peak_frequency(y[:9600], d["fs"], 80.0, 160.0)
+    f_b = peak_frequency(y[38400:], d["fs"], 160.0, 280.0)
+    assert f_b / f_a == pytest.approx(2.0 ** 0.8, rel=5e-3)
+
+
+def test_zero_depth_modulation_is_none():
+    base = W.make(alpha=3.0, n_samples=3000)
+    y = oracle.run(base)
+    for mod in ({"kind": "vibrato", "rate": 6.0, "depth": 0.0, "phase": 1.0},
+                {"kind": "gliss", "depth": 0.0, "duration": 0.5}):
+        assert np.array_equal(oracle.run(dict(base, modulation=mod)), y)
 
 
 def test_decay_rate_per_mode():
