@@ -154,6 +154,23 @@ def test_modulated_modal_recursion(mod):
     assert np.max(np.abs(y - ym)) <= 1e-9 * np.max(np.abs(ym))
 
 
+@pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 150.0, "depth": 300.0, "phase": 0.4},
+                                 {"kind": "gliss", "depth": 1.0, "duration": 0.00625}])
+@pytest.mark.parametrize("alpha,exi", [(3.0, 0), (6.0, 1)])
+def test_modulated_brute_force(mod, alpha, exi):
+    """Nonlinear strings with a fast vibrato or glissando on tiny grids: the
+    dense matrix form (Eqs. 7-9) with every gamma^2 term taken at the step's
+    gamma^n (transverse and longitudinal wave terms, phi') equals the oracle
+    to 1e-11 over 300 steps."""
+    d = W.make(f0=2500.0, alpha=alpha, kappa=1.0, excitation=EXCS[exi], modulation=mod)
+    n_t, n_l = oracle.grid(d)
+    assert n_t <= 16
+    y_o = oracle.run(d, 300)
+    g = _wave_speeds(d, 300)
+    y_b = Brute(d, n_t, n_l).run(300, gamma_fn=lambda n: g[n])
+    assert np.max(np.abs(y_o - y_b)) <= 1e-11 * np.max(np.abs(y_b))
+
+
 def test_glissando_pitch_rises_an_octave():
     """An octave glissando over 1 s: the fundamental measured near the end is
     2^0.8 times the one measured near the start (window centres 0.1 s and
