@@ -221,10 +221,12 @@ sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint6
  * sub-partitions, so this sets how many strings share an SM. */
 sfd_status sfd_batch_set_warps_per_cta(sfd_batch* b, int32_t warps_per_cta);
 
-/* Choose warps per CTA by measurement: runs probe_samples samples of every
- * string for each candidate (1, 2, 4) on throwaway copies of the strings'
- * current state (the batch's strings are not advanced), keeps the fastest
- * for the batch and returns it in *best (may be NULL). */
+/* Choose warps per CTA and warp groups by measurement: runs probe_samples
+ * samples of every string for each candidate (1, 2, 4 warps per CTA, each
+ * with warp groups off and on; see sfd_ctx_set_warp_pairs) on throwaway
+ * copies of the strings' current state (the batch's strings are not
+ * advanced), keeps the fastest for the batch and returns its warps per CTA
+ * in *best (may be NULL).  The samples do not depend on either choice. */
 sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best_warps_per_cta);
 
 /* Split form of sfd_batch_synthesize for CUDA-graph capture.  prepare

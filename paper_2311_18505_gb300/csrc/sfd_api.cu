@@ -166,6 +166,7 @@ struct sfd_batch {
   sfd_ctx* ctx = nullptr;
   std::vector<sfd_string*> strings;
   int wpc = 0;                 // warps per CTA (0: automatic)
+  int groups = -1;             // warp groups: -1 the context's setting, 0 off, 1 on (autotune)
   // prepared launch (sfd_batch_prepare / sfd_batch_launch)
   void* plan = nullptr;        // Plan*
   char* d_jobs = nullptr;      // pool block holding the plan's job table
@@ -568,7 +569,7 @@ struct Plan {
 };
 
 sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners,
-                     int wpc_override, Plan& P) {
+                     int wpc_override, Plan& P, int groups_override = -1) {
   const int nj = static_cast<int>(jobs.size());
   std::vector<int> order(nj), cls(nj);
   std::vector<double> cost(nj);
@@ -615,7 +616,7 @@ sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::
   // launch's warps stay within one per SM sub-partition, so groups only use
   // schedulers that would otherwise idle.
   for (int k = 0; k < kClasses; ++k) P.group[k] = 1;
-  if (c->warp_pairs) {
+  if (groups_override < 0 ? c->warp_pairs : groups_override) {
     int warps = nj;
     for (int k = kClasses - 2; k >= 0; --k) {
       const int n_k = P.first[k + 1] - P.first[k];
@@ -682,11 +683,11 @@ sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
 // Queue the persistent kernels for `jobs` on the context stream (job table
 // uploaded into the context's table).
 sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners,
-                       int wpc_override = 0) {
+                       int wpc_override = 0, int groups_override = -1) {
   c->last_launches = 0;
   if (jobs.empty()) return SFD_OK;
   Plan P;
-  sfd_status rc = make_plan(c, jobs, owners, wpc_override, P);
+  sfd_status rc = make_plan(c, jobs, owners, wpc_override, P, groups_override);
   if (rc) return rc;
   rc = ensure_jobs(c, static_cast<int>(P.jobs.size()));
   if (rc) return rc;
@@ -1074,7 +1075,7 @@ static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_d
     jobs.push_back(Job{b->strings[i]->d_desc, out_device + offsets[i], n_samples[i]});
     owners.push_back(b->strings[i]);
   }
-  rc = launch_jobs(c, jobs, owners, b->wpc);
+  rc = launch_jobs(c, jobs, owners, b->wpc, b->groups);
   for (auto* s : b->strings) s->started = true;
   if (rc) return rc;
   if (per_string_status) {
@@ -1145,7 +1146,7 @@ sfd_status sfd_batch_prepare(sfd_batch* b, const int64_t* n_samples, float* out_
   Plan* P = b->plan ? static_cast<Plan*>(b->plan) : new (std::nothrow) Plan();
   if (!P) return fail(SFD_ENOMEM, "host allocation failed");
   b->plan = P;
-  if ((rc = make_plan(c, jobs, owners, b->wpc, *P))) return rc;
+  if ((rc = make_plan(c, jobs, owners, b->wpc, *P, b->groups))) return rc;
   const size_t bytes = std::max<size_t>(sizeof(Job) * P->jobs.size(), sizeof(Job));
   if (bytes > b->d_jobs_bytes) {
     if (b->d_jobs) c->pool.dealloc(b->d_jobs);
@@ -1214,9 +1215,20 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best_ms = 0.f;
-  int best = 0;
+  int best = 0, best_groups = 0;
   const int candidates[3] = {1, 2, 4};
-  for (int ci = 0; ci < 3 && rc == SFD_OK; ++ci) {
+  // warp groups are a candidate only if they would form for this batch
+  bool groups_form = false;
+  {
+    std::vector<Job> jobs(n);
+    std::vector<const sfd_string*> owners(b->strings.begin(), b->strings.end());
+    Plan P;
+    if (make_plan(c, jobs, owners, 0, P, 1) == SFD_OK)
+      for (int k = 0; k < kClasses; ++k) groups_form = groups_form || P.group[k] > 1;
+  }
+  for (int cj = 0; cj < 6 && rc == SFD_OK; ++cj) {
+    const int ci = cj % 3, groups = cj / 3;   // warps per CTA x warp groups off / on
+    if (groups && !groups_form) continue;
     // fresh clones of the current state for every candidate
     std::vector<sfd_string*> cl;
     for (size_t i = 0; i < n && rc == SFD_OK; ++i) {
@@ -1234,7 +1246,7 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
       const bool timing = c->timing;
       c->timing = false;
       cudaEventRecord(e0, c->stream);
-      rc = launch_jobs(c, jobs, owners, candidates[ci]);
+      rc = launch_jobs(c, jobs, owners, candidates[ci], groups);
       cudaEventRecord(e1, c->stream);
       c->timing = timing;
       if (rc == SFD_OK) {
@@ -1242,7 +1254,7 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
-        else if (best == 0 || ms < best_ms) { best_ms = ms; best = candidates[ci]; }
+        else if (best == 0 || ms < best_ms) { best_ms = ms; best = candidates[ci]; best_groups = groups; }
       }
     }
     cudaStreamSynchronize(c->stream);
@@ -1253,6 +1265,7 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
   c->pool.dealloc(dout);
   if (rc) return rc;
   b->wpc = best;
+  b->groups = best_groups;
   if (best_warps_per_cta) *best_warps_per_cta = best;
   return SFD_OK;
 }
