@@ -224,10 +224,21 @@ def make_workload(args, rank):
         trace = W.serving_trace(args.rate, args.trace_seconds, seed=5 + 1000 * rank)
         return [d for _, d in trace], WORKLOAD_SERVING.format(rate=args.rate, secs=args.trace_seconds,
                                                               live=args.max_live)
+    split = getattr(args, "partition", "none") == "lpt"
+    seed_rank = 0 if split else rank   # a split batch is the same batch on every rank
     if args.workload == "modulated":
-        return W.batch_modulated(args.strings or 4096, seconds=args.seconds or 4.0, seed=3 + 1000 * rank), \
-            WORKLOAD_MODULATED
-    return W.batch_mixed(args.strings or 256, seconds=args.seconds or 2.0, seed=2 + 1000 * rank), WORKLOAD_NAME
+        strings = W.batch_modulated(args.strings or 4096, seconds=args.seconds or 4.0, seed=3 + 1000 * seed_rank)
+        name = WORKLOAD_MODULATED
+    else:
+        strings = W.batch_mixed(args.strings or 256, seconds=args.seconds or 2.0, seed=2 + 1000 * seed_rank)
+        name = WORKLOAD_NAME
+    if split:
+        from paper_2311_18505_gb300 import partition
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        args.batch_samples = sum(d["n_samples"] for d in strings)
+        strings = [strings[i] for i in partition.shard(strings, rank, ws)]
+        name += f"; split across {ws} ranks by cost (greedy longest processing time)"
+    return strings, name
 
 
 def run_reference(args, ws, rank):
@@ -367,7 +378,8 @@ def run_ours(args, ws, rank, local):
         del g
         free_batch(hb)
     t_total = max_over_ranks(ws, sum(times_ms) / 1e3)
-    value = ws * total * args.steps / t_total
+    split = getattr(args, "partition", "none") == "lpt"
+    value = (args.batch_samples if split else ws * total) * args.steps / t_total
     ms_step = 1e3 * t_total / args.steps
 
     # e2e through the public API with host buffers (create -> synthesize to
@@ -391,7 +403,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize(dev)
         dt = max_over_ranks(ws, time.perf_counter() - t0)
         h1, d1 = sfd.sfd_ctx_transfer_bytes(ctx)
-        e2e = {"value": ws * total * args.e2e_steps / dt, "unit": UNIT,
+        e2e = {"value": (args.batch_samples if split else ws * total) * args.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": int((h1 - h0) / args.e2e_steps),
                "d2h_bytes_per_step": int((d1 - d0) / args.e2e_steps)}
     sfd.sfd_ctx_destroy(ctx)
@@ -427,7 +439,8 @@ def run_ours(args, ws, rank, local):
                                 "sample": f"first {len(one)} strings x 24000 samples ({dt1:.1f} s wall)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name, "strings": len(strings),
                    "seconds": float(strings[0]["n_samples"] / FS), "fs": FS,
@@ -786,6 +799,9 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient",
                                                              "dataset", "single"])
     ap.add_argument("--alpha", type=float, default=1.0, help="single: stiffness-to-tension ratio (1 or 3)")
+    ap.add_argument("--partition", default="none", choices=["none", "lpt"],
+                    help="N > 1, mixed/modulated: split one batch across the ranks by cost (strong scaling) "
+                         "instead of one batch per rank (weak scaling)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: note requests per second")
     ap.add_argument("--trace-seconds", type=float, default=60.0, help="serving: length of the arrival trace")
     ap.add_argument("--max-live", type=int, default=8192, help="serving: live-note slots")

@@ -117,6 +117,13 @@ sfd_status sfd_string_create(sfd_ctx* ctx, const sfd_string_params* p, sfd_strin
 /* Grid of a string: intervals N_t, N_l and spacings h_t = 1/N_t, h_l = 1/N_l. */
 sfd_status sfd_string_info(const sfd_string* s, int32_t* n_t, int32_t* n_l, double* h_t, double* h_l);
 
+/* The grid sfd_string_create would give parameters p, without a context or a
+ * device (host arithmetic only): N_t from the stability bound of the theta
+ * scheme at the peak wave speed gamma * f0_max_ratio (Sec. 3.2, reading of
+ * the spacing rule), N_l = floor(1 / (gamma alpha k)) (h_l = gamma alpha k).
+ * Errors as sfd_string_create's parameter checks. */
+sfd_status sfd_grid(const sfd_string_params* p, int32_t* n_t, int32_t* n_l);
+
 /* Pluck (Sec. 3.3): initial condition u^0 = u^1 = triangle of peak amp/L at
  * pos (fraction of L), zero initial velocity.  Valid only before the first
  * synthesize call (else SFD_ESTATE). */

@@ -805,6 +805,19 @@ sfd_status sfd_ctx_set_timing(sfd_ctx* c, int32_t enable) {
   return SFD_OK;
 }
 
+sfd_status sfd_grid(const sfd_string_params* p, int32_t* n_t, int32_t* n_l) {
+  if (!p || !n_t || !n_l) return fail(SFD_EINVAL, "NULL argument");
+  sfd_string_params q = *p;
+  double gamma = 0;
+  sfd_status rc = normalize_params(q, &gamma);
+  if (rc) return rc;
+  int nt = 0, nl = 0;
+  if ((rc = derive_grid(q, gamma * q.f0_max_ratio, &nt, &nl))) return rc;
+  *n_t = nt;
+  *n_l = nl;
+  return SFD_OK;
+}
+
 sfd_status sfd_ctx_set_warp_pairs(sfd_ctx* c, int32_t enable) {
   if (!c) return fail(SFD_EINVAL, "ctx is NULL");
   c->warp_pairs = enable != 0;

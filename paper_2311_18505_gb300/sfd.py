@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         "sfd_ctx_memory": (i32, [vp, P(ctypes.c_size_t), P(ctypes.c_size_t)]),
         "sfd_string_create": (i32, [vp, P(sfd_string_params), P(vp)]),
         "sfd_string_info": (i32, [vp, P(i32), P(i32), P(dbl), P(dbl)]),
+        "sfd_grid": (i32, [P(sfd_string_params), P(i32), P(i32)]),
         "sfd_excite_pluck": (i32, [vp, dbl, dbl]),
         "sfd_excite_hammer": (i32, [vp, dbl, dbl, dbl, dbl, dbl]),
         "sfd_excite_bow": (i32, [vp, dbl, dbl, dbl, dbl, dbl, dbl]),
@@ -182,6 +183,13 @@ def sfd_string_create(ctx: int, params: sfd_string_params) -> int:
     h = ctypes.c_void_p()
     _check(lib().sfd_string_create(ctx, ctypes.byref(params), ctypes.byref(h)))
     return h.value
+
+
+def sfd_grid(params: sfd_string_params) -> tuple[int, int]:
+    """(N_t, N_l) of a string with these parameters; host arithmetic, no device."""
+    nt, nl = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sfd_grid(ctypes.byref(params), ctypes.byref(nt), ctypes.byref(nl)))
+    return nt.value, nl.value
 
 
 def sfd_string_info(s: int) -> tuple[int, int, float, float]:

@@ -127,3 +127,42 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
+
+
+def test_host_grid_matches_the_oracle():
+    """sfd_grid (host arithmetic, no device) gives the oracle's grid for
+    random strings, modulated or not, and refuses invalid parameters."""
+    import numpy as np
+    import oracle
+    from paper_2311_18505_gb300 import sfd
+    from paper_2311_18505_gb300 import workloads as W
+    rng = np.random.default_rng(3)
+    for i in range(200):
+        d = W.random_string(rng, f0_lo=30.0, f0_hi=2000.0, seconds=0.01)
+        if i % 2:
+            d["modulation"] = {"kind": "vibrato", "rate": 6.0, "depth": 30.0, "phase": 0.0}
+        assert sfd.sfd_grid(sfd.params_from_dict(d)) == oracle.grid(d)
+    p = sfd.params_from_dict(W.make())
+    p.alpha = 0.5
+    with pytest.raises(sfd.SfdError) as ei:
+        sfd.sfd_grid(p)
+    assert ei.value.code == sfd.SFD_EINVAL
+
+
+def test_lpt_partition():
+    """Every string on exactly one rank, the same split however often it is
+    computed, and the greedy bound: no rank above the mean load plus the
+    largest single cost."""
+    from paper_2311_18505_gb300 import partition
+    from paper_2311_18505_gb300 import workloads as W
+    strings = W.batch_modulated(512, seconds=0.5, seed=3)
+    costs = [partition.string_cost(d) for d in strings]
+    for world in (1, 2, 3, 8):
+        parts = partition.partition_lpt(costs, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(strings)))
+        assert parts == partition.partition_lpt(costs, world)
+        loads = [sum(costs[i] for i in p) for p in parts]
+        assert max(loads) <= sum(costs) / world + max(costs)
+        assert [partition.shard(strings, r, world) for r in range(world)] == parts
+    with pytest.raises(ValueError):
+        partition.partition_lpt(costs, 0)

@@ -42,9 +42,13 @@ def _bench_rank(rank, port, out):
         m = bench.max_over_ranks(ws, 1.5 + rank)
         args = bench.parse_args(["--gpus", str(WORLD)])
         strings, _ = bench.make_workload(args, rank)
+        split_args = bench.parse_args(["--gpus", str(WORLD), "--partition", "lpt", "--strings", "64",
+                                       "--seconds", "0.5"])
+        split, _ = bench.make_workload(split_args, rank)
         ref = bench.run_reference(bench.parse_args(["--impl", "reference"]), ws, rank) if rank else None
         with open(os.path.join(out, f"bench{rank}.json"), "w") as f:
-            json.dump({"max": m, "f0": [d["f0"] for d in strings], "ref": ref}, f)
+            json.dump({"max": m, "f0": [d["f0"] for d in strings], "ref": ref,
+                       "split": [d["f0"] for d in split], "batch_samples": split_args.batch_samples}, f)
     finally:
         dist.destroy_process_group()
 
@@ -58,6 +62,13 @@ def test_bench_rank_helpers(tmp_path):
     assert not set(got[0]["f0"]) & set(got[1]["f0"])
     # the reference arm runs on rank 0 alone; the others return without work
     assert got[1]["ref"] == 0
+    # --partition lpt: one 64-string batch split between the ranks, every
+    # string on exactly one of them
+    from paper_2311_18505_gb300 import workloads as W
+    whole = W.batch_mixed(64, seconds=0.5, seed=2)
+    assert sorted(got[0]["split"] + got[1]["split"]) == sorted(d["f0"] for d in whole)
+    assert not set(got[0]["split"]) & set(got[1]["split"])
+    assert got[0]["batch_samples"] == got[1]["batch_samples"] == sum(d["n_samples"] for d in whole)
 
 
 def _dataset_rank(rank, port, out):
