@@ -361,8 +361,8 @@ sfd_status sfd_server_destroy(sfd_server* sv);
  * Gradients of a waveform loss with respect to string parameters, by the
  * discrete adjoint of the time-stepping (no counterpart in the paper).
  *
- * A tape holds n strings (params[i], exc[i]: pluck, hammer or bow, no f0
- * modulation) synthesized for n_samples each.  sfd_tape_forward writes the
+ * A tape holds n strings (params[i], exc[i]: pluck, hammer or bow, mod[i]:
+ * f0 modulation, or mod = NULL for none) synthesized for n_samples each.  sfd_tape_forward writes the
  * audio y (device, y[i * n_samples + j], metres) and keeps every string's
  * state every checkpoint_every samples.  sfd_tape_backward takes dJ/dy
  * (device, same layout) and writes, per string, dJ/d(kappa, alpha, sigma0,
@@ -380,8 +380,15 @@ sfd_status sfd_server_destroy(sfd_server* sv);
  * --------------------------------------------------------------------- */
 typedef struct sfd_tape sfd_tape;
 #define SFD_GRAD_PARAMS 5
+/* f0 modulation of a string, as sfd_set_modulation takes it. */
+typedef struct {
+  int32_t kind;             /* SFD_MOD_NONE / VIBRATO / GLISS */
+  int32_t pad_;
+  double rate_hz, depth, phase_rad, duration_s;
+} sfd_modulation;
 sfd_status sfd_tape_create(sfd_ctx* ctx, int32_t n, const sfd_string_params* params, const sfd_excitation* exc,
-                           int64_t n_samples, int32_t checkpoint_every, sfd_tape** out);
+                           const sfd_modulation* mod, int64_t n_samples, int32_t checkpoint_every,
+                           sfd_tape** out);
 /* Runs from the initial state every time; returns SFD_EUNSTABLE / SFD_ENOCONV
  * (audio written) if a string's synthesis reported one. */
 sfd_status sfd_tape_forward(sfd_tape* t, float* y_device);

@@ -76,8 +76,19 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const bool hammer = Dp->exc == kHammer;
   const int RU = kWarp * m_u + 4, RZ = has_z ? kWarp * m_z + 4 : 0;
   const R dg = Dp->dg, og = Dp->og, s0 = Dp->s0, s0u = Dp->s0u, s1 = Dp->s1, s1l = Dp->s1l;
-  const R lam2 = static_cast<R>(Dp->lam2) + static_cast<R>(Dp->lam2_lo), mu2 = Dp->mu2, lam2l = Dp->lam2l;
-  const R ca = Dp->ca, cb = Dp->cb, cz = Dp->cz;
+  const R mu2 = Dp->mu2;
+  // the gamma^2 coefficients of the step being reversed: with f0 modulation
+  // the forward scales them by rm = (gamma^n / gamma)^2 each step, and they
+  // are formed here from the same FP32 expressions (so the adjoint is that
+  // of the forward's own arithmetic); rmd carries rm into the gradients of
+  // the unscaled coefficients
+  const float lam2_0f = Dp->lam2, lam2lo_0f = Dp->lam2_lo, lam2l_0f = Dp->lam2l;
+  const float ca_0f = Dp->ca, cb_0f = Dp->cb, cz_0f = Dp->cz;
+  const int mod_kind = Dp->mod_kind;
+  const double mod_inc = Dp->mod_inc, mod_phase0 = Dp->mod_phase0;
+  const float mod_depth2 = Dp->mod_depth2;
+  R lam2 = static_cast<R>(lam2_0f) + static_cast<R>(lam2lo_0f), lam2l = lam2l_0f;
+  R ca = ca_0f, cb = cb_0f, cz = cz_0f, rmd = 1.0;
   const R bsgn = Dp->boundary == 1 ? -1.0 : 1.0;
   const int en = Dp->e_node, on = Dp->o_node;
   const R ew = Dp->e_w, js = Dp->jscale, ow = Dp->o_w, oscale = Dp->out_scale;
@@ -311,6 +322,23 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
 
   for (int64_t m = J.m_end; m > J.m_start; --m) {
     const int64_t n = m - 1;
+    if (mod_kind != 0) {   // the step n -> n + 1 as the forward took it
+      float rm = 1.f;
+      if (mod_kind == 1) {
+        double t = fma(static_cast<double>(n), mod_inc, mod_phase0);
+        t -= floor(t);
+        rm = exp2f(mod_depth2 * sinf(6.28318530717958647f * static_cast<float>(t)));
+      } else if (mod_kind == 2) {
+        rm = exp2f(static_cast<float>(mod_inc * static_cast<double>(n)));
+      }
+      const float l2 = lam2_0f * rm;
+      lam2 = static_cast<R>(l2) + static_cast<R>(fmaf(lam2_0f, rm, -l2) + lam2lo_0f * rm);
+      lam2l = static_cast<R>(lam2l_0f * rm);
+      ca = static_cast<R>(ca_0f * rm);
+      cb = static_cast<R>(cb_0f * rm);
+      cz = static_cast<R>(cz_0f * rm);
+      rmd = static_cast<R>(rm);
+    }
     add_output(J.dy[m], false);
     // ---- level n state; a = D(n+1) - D(n) etc. ----
     float uh, dh;
@@ -494,6 +522,13 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       pg[kGAmp] += vb == 0.0 ? -nus : -kk * kk * bF * phid * nus;
     }
     __syncwarp();
+    if (mod_kind != 0) {   // d(coefficient of step n) / d(unscaled coefficient) = rm
+      pg[kGLam2] *= rmd;
+      pg[kGLam2l] *= rmd;
+      pg[kGCa] *= rmd;
+      pg[kGCb] *= rmd;
+      pg[kGCz] *= rmd;
+    }
 #pragma unroll
     for (int k = 0; k < kGradSlots; ++k) acc[k] += pg[k];
     // the level-n D becomes the next step's D(n+1)

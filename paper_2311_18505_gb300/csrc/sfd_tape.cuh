@@ -80,7 +80,8 @@ int64_t seg_start_level(const sfd_tape* t, int c) { return c == 0 ? 1 : static_c
 extern "C" {
 
 sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* params, const sfd_excitation* exc,
-                           int64_t n_samples, int32_t checkpoint_every, sfd_tape** out) {
+                           const sfd_modulation* mod, int64_t n_samples, int32_t checkpoint_every,
+                           sfd_tape** out) {
   if (!c || !params || !exc || !out) return fail(SFD_EINVAL, "NULL argument");
   *out = nullptr;
   if (n <= 0 || n_samples < 2 || checkpoint_every < 2)
@@ -107,6 +108,10 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
          : e.kind == kHammer ? sfd_excite_hammer(s, e.mass_kg, e.vel_mps, e.pos, e.omega_h, e.alpha_h)
                              : sfd_excite_bow(s, e.vel_mps, e.force_n, e.pos, e.a_s_per_m, e.eps, e.release_time_s);
     if (rc) break;
+    if (mod && mod[i].kind != SFD_MOD_NONE) {
+      rc = sfd_set_modulation(s, mod[i].kind, mod[i].rate_hz, mod[i].depth, mod[i].phase_rad, mod[i].duration_s);
+      if (rc) break;
+    }
     sfd_string* r = nullptr;
     rc = clone_string(s, &r);
     if (rc) break;

@@ -3,7 +3,8 @@ tape (``sfd_tape_*``).
 
 ``synthesize(theta, strings, n_samples)`` renders the strings with the
 parameters of ``theta`` (one row per string: kappa, alpha, sigma0, sigma1,
-amplitude -- the pluck amplitude in metres or the hammer velocity in m/s)
+amplitude -- the pluck amplitude in metres, the hammer or the bow velocity
+in m/s; strings may be f0-modulated and read on either output channel)
 and returns the audio ``(n, n_samples)`` on the GPU; ``backward`` runs the
 hand-written discrete adjoint kernel (checkpoints every ``checkpoint_every``
 samples, each segment recomputed from its checkpoint).  Gradients hold each

@@ -58,6 +58,14 @@ class sfd_excitation(ctypes.Structure):
 SFD_NOALLOC_SCRATCH_BYTES = 32 * 1024
 
 
+class sfd_modulation(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("rate_hz", ctypes.c_double), ("depth", ctypes.c_double),
+        ("phase_rad", ctypes.c_double), ("duration_s", ctypes.c_double),
+    ]
+
+
 class sfd_request(ctypes.Structure):
     _fields_ = [
         ("params", sfd_string_params), ("exc", sfd_excitation),
@@ -132,7 +140,8 @@ def lib() -> ctypes.CDLL:
         "sfd_server_clock": (dbl, [vp]),
         "sfd_server_stats_get": (i32, [vp, P(sfd_server_stats)]),
         "sfd_server_destroy": (i32, [vp]),
-        "sfd_tape_create": (i32, [vp, i32, P(sfd_string_params), P(sfd_excitation), i64, i32, P(vp)]),
+        "sfd_tape_create": (i32, [vp, i32, P(sfd_string_params), P(sfd_excitation), P(sfd_modulation), i64, i32,
+                                  P(vp)]),
         "sfd_tape_forward": (i32, [vp, vp]),
         "sfd_tape_backward": (i32, [vp, vp, P(dbl)]),
         "sfd_tape_destroy": (i32, [vp]),
@@ -435,14 +444,25 @@ SFD_GRAD_PARAMS = 5
 GRAD_PARAM_NAMES = ("kappa", "alpha", "sigma0", "sigma1", "amplitude")
 
 
+def modulation_from_dict(mod: dict | None) -> sfd_modulation:
+    m = sfd_modulation()
+    mod = mod or {"kind": "none"}
+    if mod["kind"] == "vibrato":
+        m.kind, m.rate_hz, m.depth, m.phase_rad = SFD_MOD_VIBRATO, mod["rate"], mod["depth"], mod.get("phase", 0.0)
+    elif mod["kind"] == "gliss":
+        m.kind, m.depth, m.duration_s = SFD_MOD_GLISS, mod["depth"], mod["duration"]
+    return m
+
+
 def sfd_tape_create(ctx: int, strings, n_samples: int, checkpoint_every: int = 1024) -> int:
-    """Tape of plucked or hammered strings (parameter dicts, no modulation; either
+    """Tape of strings (parameter dicts: any excitation, f0 modulation and
     output channel)."""
     n = len(strings)
     params = (sfd_string_params * n)(*[params_from_dict(d) for d in strings])
     excs = (sfd_excitation * n)(*[excitation_from_dict(d["excitation"]) for d in strings])
+    mods = (sfd_modulation * n)(*[modulation_from_dict(d.get("modulation")) for d in strings])
     out = ctypes.c_void_p()
-    _check(lib().sfd_tape_create(ctx, n, params, excs, n_samples, checkpoint_every, ctypes.byref(out)))
+    _check(lib().sfd_tape_create(ctx, n, params, excs, mods, n_samples, checkpoint_every, ctypes.byref(out)))
     return out.value
 
 

@@ -216,6 +216,44 @@ def test_vector_jacobian_product_longitudinal_output(sfd, ctx):
     assert checked >= 6
 
 
+@pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 6.0, "depth": 40.0, "phase": 0.3},
+                                 {"kind": "gliss", "depth": 0.5, "duration": 0.1}])
+def test_vector_jacobian_product_modulated(sfd, ctx, mod):
+    """f0-modulated strings: the adjoint scales each step's gamma^2
+    coefficients as the forward did, and the gradient of each unscaled
+    coefficient carries the step's factor.  Same check as for unmodulated
+    strings (the oracle's central differences on the grid sized for the
+    modulation's peak)."""
+    base, target = workload(6, N_SHORT)
+    base = [dict(d, modulation=mod) for d in base]
+    target = [dict(d, modulation=mod) for d in target]
+    tgt = targets_of(target, N_SHORT)
+    tape = sfd.sfd_tape_create(ctx, base, N_SHORT, 1024)
+    try:
+        y = torch.empty(len(base), N_SHORT, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        w = (2.0 * (y.double() - torch.from_numpy(tgt).cuda())).float().contiguous()
+        g = sfd.sfd_tape_backward(tape, w, len(base))
+        yt = y.cpu().numpy()
+    finally:
+        sfd.sfd_tape_destroy(tape)
+    for d, row in zip(base, yt):   # the tape's forward is the plain modulated synthesis
+        s = sfd.string_from_dict(ctx, d)
+        assert np.array_equal(row, sfd.sfd_synthesize(s, N_SHORT))
+        sfd.sfd_string_destroy(s)
+    w = w.double().cpu().numpy()
+    from paper_2311_18505_gb300.grad import params_of
+    for i, d in enumerate(base):
+        nt, nl = oracle.grid(d)
+        th = np.array(params_of(d))
+        runs = [dict(perturbed(d, k, f), n_t=nt, n_l=nl) for k in range(5) for f in (1 + 1e-6, 1 - 1e-6)]
+        ys, _ = oracle.run_batch(runs, n_samples=N_SHORT)
+        ref = np.array([(w[i] @ ys[2 * k] - w[i] @ ys[2 * k + 1]) / (2e-6 * th[k]) for k in range(5)])
+        scale = np.max(np.abs(ref * th))
+        err = np.abs(g[i] - ref) * th
+        assert np.all(err <= 1e-4 * scale + 2e-3 * np.abs(ref * th)), (i, g[i], ref)
+
+
 def _bow(vel, force, pos=0.21, a=100.0, eps=0.1):
     return {"kind": "bow", "vel": vel, "force": force, "pos": pos, "a": a, "eps": eps, "release": -1.0}
 

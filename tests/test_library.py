@@ -110,7 +110,7 @@ def test_binding_structs_match_the_header(tmp_path):
         pytest.skip("no host C compiler")
     structs = {"sfd_string_params": sfd.sfd_string_params, "sfd_excitation": sfd.sfd_excitation,
                "sfd_request": sfd.sfd_request, "sfd_chunk": sfd.sfd_chunk,
-               "sfd_server_stats": sfd.sfd_server_stats}
+               "sfd_server_stats": sfd.sfd_server_stats, "sfd_modulation": sfd.sfd_modulation}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sfd.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
