@@ -47,7 +47,9 @@ class Spec(ctypes.Structure):
         ("mod_kind", ctypes.c_int32), ("pad1", ctypes.c_int32),
         ("mod_rate", ctypes.c_double), ("mod_depth", ctypes.c_double),
         ("mod_phase", ctypes.c_double), ("mod_duration", ctypes.c_double),
-        ("out_channel", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("out_channel", ctypes.c_int32), ("bow_env_n", ctypes.c_int32),
+        ("bow_env_t", ctypes.c_double * 16), ("bow_env_v", ctypes.c_double * 16),
+        ("bow_env_f", ctypes.c_double * 16), ("bow_env_x", ctypes.c_double * 16),
     ]
 
 
@@ -130,6 +132,15 @@ def spec(d: dict, n_t: int = 0, n_l: int = 0) -> Spec:
         s.bow_vel, s.bow_force, s.bow_pos = ex["vel"], ex["force"], ex["pos"]
         s.bow_a, s.bow_eps = ex.get("a", 100.0), ex.get("eps", 0.1)
         s.bow_release = ex.get("release", -1.0)
+        env = ex.get("envelope")
+        if env:   # time-varying controls: breakpoint times and values (constant where a key is absent)
+            t = list(env["t"])
+            s.bow_env_n = len(t)
+            for j, tj in enumerate(t):
+                s.bow_env_t[j] = tj
+                s.bow_env_v[j] = env["vel"][j] if "vel" in env else ex["vel"]
+                s.bow_env_f[j] = env["force"][j] if "force" in env else ex["force"]
+                s.bow_env_x[j] = env["pos"][j] if "pos" in env else ex["pos"]
     s.mod_kind = MOD[mod.get("kind", "none")]
     if s.mod_kind == 1:
         s.mod_rate, s.mod_depth, s.mod_phase = mod["rate"], mod["depth"], mod.get("phase", 0.0)

@@ -140,6 +140,27 @@ static double interp(const sfdo_string* S, const double* u, const int node[2], c
   return w[0] * U(S, u, node[0]) + w[1] * U(S, u, node[1]);
 }
 
+/* Bow controls at time t from the breakpoint envelopes (Sec. 3.3.1 makes
+ * v_B, F_B and x_B time-varying): linear between breakpoints, the first or
+ * last value outside them. */
+static void bow_controls(const sfdo_spec* P, double t, double* v, double* f, double* x) {
+  const int m = P->bow_env_n;
+  if (t <= P->bow_env_t[0] || m == 1) {
+    *v = P->bow_env_v[0]; *f = P->bow_env_f[0]; *x = P->bow_env_x[0];
+    return;
+  }
+  if (t >= P->bow_env_t[m - 1]) {
+    *v = P->bow_env_v[m - 1]; *f = P->bow_env_f[m - 1]; *x = P->bow_env_x[m - 1];
+    return;
+  }
+  int j = 0;
+  while (j + 1 < m - 1 && t >= P->bow_env_t[j + 1]) ++j;
+  const double r = (t - P->bow_env_t[j]) / (P->bow_env_t[j + 1] - P->bow_env_t[j]);
+  *v = P->bow_env_v[j] + r * (P->bow_env_v[j + 1] - P->bow_env_v[j]);
+  *f = P->bow_env_f[j] + r * (P->bow_env_f[j + 1] - P->bow_env_f[j]);
+  *x = P->bow_env_x[j] + r * (P->bow_env_x[j + 1] - P->bow_env_x[j]);
+}
+
 /* f0 modulation (abstract; Sec. 1 lists f0 modulation among the
  * stochastic parameters).  gamma^n for the step n -> n+1. */
 static double gamma_at(const sfdo_string* S, int64_t n) {
@@ -306,6 +327,11 @@ sfdo_string* sfdo_create(const sfdo_spec* s) {
         s->bow_a >= 0))
     return NULL;
   if (s->exc_kind == SFDO_EXC_PLUCK && !(s->pluck_pos > 0 && s->pluck_pos < 1)) return NULL;
+  if (s->bow_env_n < 0 || s->bow_env_n > 16) return NULL;
+  for (int j = 0; j < s->bow_env_n; ++j) {
+    if (!(s->bow_env_x[j] > 0 && s->bow_env_x[j] < 1 && s->bow_env_f[j] >= 0)) return NULL;
+    if (j > 0 && !(s->bow_env_t[j] > s->bow_env_t[j - 1])) return NULL;
+  }
   sfdo_string* S = calloc(1, sizeof(sfdo_string));
   S->p = *s;
   S->nt = nt; S->nl = nl;
@@ -573,9 +599,15 @@ static int step(sfdo_string* S) {
   double force = 0.0;               /* normalised force on the string      */
   if (P->exc_kind == SFDO_EXC_BOW) {
     const double t = (double)S->n * k;
+    double bv = P->bow_vel, bf = P->bow_force;
+    if (P->bow_env_n > 0) {   /* time-varying controls: the step's values, and I, J at x_B(t) */
+      double bx = P->bow_pos;
+      bow_controls(P, t, &bv, &bf, &bx);
+      interp_weights(S, bx, S->e_node, S->e_w);
+    }
     const double FB = (P->bow_release >= 0 && t >= P->bow_release) ? 0.0
-                      : P->bow_force / (P->rho_a * P->length * P->length);
-    const double vB = P->bow_vel / P->length, aN = P->bow_a * P->length;
+                      : bf / (P->rho_a * P->length * P->length);
+    const double vB = bv / P->length, aN = P->bow_a * P->length;
     /* unit-force response A z = J (same factors) */
     memset(S->zsol, 0, sizeof(double) * S->ntot);
     for (int a = 0; a < 2; ++a) {

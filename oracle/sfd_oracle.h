@@ -77,7 +77,11 @@ typedef struct {
   double mod_phase;       /* vibrato phase [rad]                                */
   double mod_duration;    /* glissando duration [s]                             */
   int32_t out_channel;    /* 0: transverse u, 1: longitudinal zeta (Sec. 4.2)   */
-  int32_t pad2;
+  int32_t bow_env_n;      /* bow: breakpoints of the control envelopes (0: none) */
+  /* Time-varying bow controls (Sec. 3.3.1): breakpoint times [s] and v_B
+   * [m/s], F_B [N], x_B at them; the step n -> n+1 takes the values at
+   * t = n k, linear between breakpoints and held outside them. */
+  double bow_env_t[16], bow_env_v[16], bow_env_f[16], bow_env_x[16];
 } sfdo_spec;
 
 typedef struct sfdo_string sfdo_string;

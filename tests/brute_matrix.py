@@ -162,11 +162,18 @@ class Brute:
         d, k = self.d, self.k
         ex = d["excitation"]
         L = d_len(d)
-        FB = ex["force"] / (d["rho_a"] * L * L)
+        force, vel, pos = ex["force"], ex["vel"], ex["pos"]
+        env = ex.get("envelope")
+        if env:   # controls at t = n k, piecewise linear, held outside the breakpoints
+            t = n * k
+            force = np.interp(t, env["t"], env["force"]) if "force" in env else force
+            vel = np.interp(t, env["t"], env["vel"]) if "vel" in env else vel
+            pos = np.interp(t, env["t"], env["pos"]) if "pos" in env else pos
+        FB = force / (d["rho_a"] * L * L)
         if ex.get("release", -1.0) >= 0 and n * k >= ex["release"]:
             FB = 0.0
-        vB, aN, eps = ex["vel"] / L, ex["a"] * L, ex["eps"]
-        Ib = np.concatenate([self.interp_row(ex["pos"]), np.zeros(self.nz)])
+        vB, aN, eps = vel / L, ex["a"] * L, ex["eps"]
+        Ib = np.concatenate([self.interp_row(pos), np.zeros(self.nz)])
         J = Ib / self.ht
 
         def w_of(phi):

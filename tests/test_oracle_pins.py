@@ -171,6 +171,33 @@ def test_modulated_brute_force(mod, alpha, exi):
     assert np.max(np.abs(y_o - y_b)) <= 1e-11 * np.max(np.abs(y_b))
 
 
+BOW_ENV = {"t": [0.0, 0.002, 0.004, 0.006], "vel": [0.1, 0.4, 0.25, 0.3], "force": [0.5, 2.0, 1.0, 0.0],
+           "pos": [0.15, 0.3, 0.45, 0.2]}
+
+
+@pytest.mark.parametrize("alpha", [1.0, 4.0])
+def test_bow_envelope_brute_force(alpha):
+    """Time-varying bow velocity, force and position (Sec. 3.3.1): the dense
+    matrix form with the controls of step n at t = n k (linear between
+    breakpoints) and I, J at the step's x_B equals the oracle to 1e-11."""
+    ex = dict(EXCS[2], release=-1.0, envelope=BOW_ENV)
+    d = W.make(f0=2500.0, alpha=alpha, kappa=1.0, excitation=ex)
+    n_t, n_l = oracle.grid(d)
+    y_o = oracle.run(d, 400)
+    y_b = Brute(d, n_t, n_l).run(400)
+    assert np.max(np.abs(y_o - y_b)) <= 1e-11 * np.max(np.abs(y_b))
+    # the envelope matters: constant controls give another waveform
+    y_c = oracle.run(dict(d, excitation=EXCS[2]), 400)
+    assert np.max(np.abs(y_o - y_c)) > 1e-3 * np.max(np.abs(y_o))
+
+
+def test_constant_bow_envelope_is_no_envelope():
+    ex = EXCS[2]
+    flat = {"t": [0.0, 0.01], "vel": [ex["vel"]] * 2, "force": [ex["force"]] * 2, "pos": [ex["pos"]] * 2}
+    d = W.make(alpha=3.0, f0=196.0, excitation=ex, n_samples=2000)
+    assert np.array_equal(oracle.run(dict(d, excitation=dict(ex, envelope=flat))), oracle.run(d))
+
+
 def test_glissando_pitch_rises_an_octave():
     """An octave glissando over 1 s: the fundamental measured near the end is
     2^0.8 times the one measured near the start (window centres 0.1 s and
