@@ -143,6 +143,19 @@ sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, doub
 sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double pos,
                           double a_s_per_m, double eps, double release_time_s);
 
+/* Time-varying bow controls (Sec. 3.3.1 makes the bow velocity, force and
+ * position control parameters that vary in time): after sfd_excite_bow and
+ * before the first synthesis, n_points (1..16) breakpoints at times t_s[j]
+ * (seconds from the start, increasing) with vel_mps[j] [m/s], force_n[j]
+ * [N] and pos[j] (fraction of L, in (0, 1)); a NULL array keeps that
+ * control at its sfd_excite_bow value.  The step n -> n+1 takes the values
+ * at t = n / fs: linear between breakpoints, the first or last value
+ * outside them; the interpolation I and spreading J of the bow follow pos.
+ * The release time of sfd_excite_bow still sets the force to zero.  Errors:
+ * SFD_EINVAL (not bowed, bad values), SFD_ESTATE (already started). */
+sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, const double* vel_mps,
+                            const double* force_n, const double* pos);
+
 /* f0 modulation (Sec. 1): kind SFD_MOD_VIBRATO, gamma^n = gamma 2^{(c/1200)
  * sin(2 pi rate t + phase)} with depth c in cents; SFD_MOD_GLISS, gamma^n =
  * gamma 2^{D t / duration} with depth D in octaves.  The grid must have been

@@ -160,6 +160,7 @@ struct sfd_string {
   int exc = kPluck;
   double pluck_amp = 0, pluck_pos = 0.5;
   double hammer_uh1 = 0;    // u_H^1 = v_H k (normalised), u_H^0 = 0
+  double bow_pos = 0.5;     // x_B of sfd_excite_bow (constant position of an envelope)
 };
 
 struct sfd_batch {
@@ -939,6 +940,8 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   s->h.bow_v = static_cast<float>(vel_mps / p.length_m);
   s->h.bow_a = static_cast<float>(a_s_per_m * p.length_m);
   s->h.bow_eps = static_cast<float>(eps);
+  s->h.bow_env_n = 0;   // constant controls until sfd_bow_envelope
+  s->bow_pos = pos;
   if (release_time_s >= 0) {
     // first step n with n k >= release (same comparison as stated in Eq. 5's use)
     int64_t n = static_cast<int64_t>(std::ceil(release_time_s * p.fs));
@@ -951,6 +954,37 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
   return upload_initial(s);
+}
+
+sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, const double* vel_mps,
+                            const double* force_n, const double* pos) {
+  if (!s || !t_s) return fail(SFD_EINVAL, "NULL argument");
+  if (s->started) return fail(SFD_ESTATE, "set the bow envelope before synthesizing");
+  if (s->exc != kBow) return fail(SFD_EINVAL, "the string is not bowed (call sfd_excite_bow first)");
+  if (n_points < 1 || n_points > 16) return fail(SFD_EINVAL, "1 to 16 breakpoints");
+  const sfd_string_params& p = s->p;
+  Desc& D = s->h;
+  for (int j = 0; j < n_points; ++j) {
+    if (!std::isfinite(t_s[j]) || (j > 0 && !(t_s[j] > t_s[j - 1])))
+      return fail(SFD_EINVAL, "breakpoint times must increase");
+    if (vel_mps && !std::isfinite(vel_mps[j])) return fail(SFD_EINVAL, "bad bow velocity");
+    if (force_n && !(force_n[j] >= 0)) return fail(SFD_EINVAL, "bow force must be >= 0");
+    if (pos && !(pos[j] > 0 && pos[j] < 1)) return fail(SFD_EINVAL, "bow position must be in (0, 1)");
+  }
+  // constant controls where an array is NULL: the values of sfd_excite_bow
+  const double x0 = s->bow_pos;
+  for (int j = 0; j < n_points; ++j) {
+    D.bow_env_t[j] = t_s[j] * p.fs;
+    D.bow_env_v[j] = vel_mps ? static_cast<float>(vel_mps[j] / p.length_m) : D.bow_v;
+    D.bow_env_f[j] = force_n ? static_cast<float>(force_n[j] / (p.linear_density * p.length_m * p.length_m)) : D.bow_F;
+    D.bow_env_x[j] = pos ? static_cast<float>(pos[j]) : static_cast<float>(x0);
+  }
+  D.bow_env_n = n_points;
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
+  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return SFD_OK;
 }
 
 sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth, double phase_rad,

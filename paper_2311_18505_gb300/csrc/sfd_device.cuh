@@ -193,6 +193,34 @@ __device__ __forceinline__ float zinterp(const float* __restrict__ A, int node, 
   return (1.f - w) * a + w * b;
 }
 
+// Bow controls of step n from the descriptor's breakpoint envelopes
+// (breakpoints in steps): linear between breakpoints, the first or last
+// value outside them; x is the bow position, from which the step's
+// interpolation node and weight (node, w) follow as for a fixed point.
+__device__ __forceinline__ void bow_env_eval(const Desc* __restrict__ D, int64_t n, float& v, float& f, int& node,
+                                             float& w) {
+  const int m = D->bow_env_n;
+  const double t = static_cast<double>(n);
+  double x;
+  if (m == 1 || t <= D->bow_env_t[0]) {
+    v = D->bow_env_v[0]; f = D->bow_env_f[0]; x = D->bow_env_x[0];
+  } else if (t >= D->bow_env_t[m - 1]) {
+    v = D->bow_env_v[m - 1]; f = D->bow_env_f[m - 1]; x = D->bow_env_x[m - 1];
+  } else {
+    int j = 0;
+    while (j + 1 < m - 1 && t >= D->bow_env_t[j + 1]) ++j;
+    const double r = (t - D->bow_env_t[j]) / (D->bow_env_t[j + 1] - D->bow_env_t[j]);
+    v = static_cast<float>(D->bow_env_v[j] + r * (static_cast<double>(D->bow_env_v[j + 1]) - D->bow_env_v[j]));
+    f = static_cast<float>(D->bow_env_f[j] + r * (static_cast<double>(D->bow_env_f[j + 1]) - D->bow_env_f[j]));
+    x = D->bow_env_x[j] + r * (static_cast<double>(D->bow_env_x[j + 1]) - D->bow_env_x[j]);
+  }
+  const double pos = x * D->n_t;
+  int l = static_cast<int>(floor(pos));
+  l = l < 0 ? 0 : (l > D->n_t - 1 ? D->n_t - 1 : l);
+  node = l;
+  w = static_cast<float>(pos - l);
+}
+
 // Bow friction: solve v + c phi(v) = b with phi(v) = sign(v)(eps + (1-eps)
 // e^{-a|v|}) (Sec. 3.3.1, Eq. 5).  Sticking (v = 0, phi = b/c) whenever
 // |b| <= c; otherwise the root of the convex g(w) = w + c phi(w) - |b| on

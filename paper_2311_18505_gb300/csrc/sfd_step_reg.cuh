@@ -462,8 +462,11 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
     CP0[r] = CPr[r];
   }
   const bool forced = exc != kPluck;
-  const int en = Dp->e_node;
-  const float ew = Dp->e_w, js = Dp->jscale;
+  int en = Dp->e_node;              // excitation point (a bow envelope moves it per step)
+  float ew = Dp->e_w;
+  const float js = Dp->jscale;
+  const int benv = exc == kBow ? Dp->bow_env_n : 0;
+  float bv = bow_v;                 // the step's bow velocity
   float XP[MU];
   auto load_J = [&](float (&E)[MU]) {
 #pragma unroll
@@ -530,7 +533,17 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
         eta = uh - node_interp<MU>(U, en, ew, n_u);
         if (eta > 0.f) k2G = ham_k2w * powf(eta, ham_expo);
       } else if (exc == kBow) {
-        FB = (n < bow_release_n) ? bow_F : 0.f;
+        float bf = bow_F;
+        if (benv > 0) {
+          const int en0 = en;
+          const float ew0 = ew;
+          bow_env_eval(Dp, n, bv, bf, en, ew);
+          if (linear && (en != en0 || ew != ew0)) {   // the fixed-matrix response A^-1 J follows x_B
+            load_J(XP);
+            tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, XP, XP, lane, rdu);
+          }
+        }
+        FB = (n < bow_release_n) ? bf : 0.f;
       }
       const bool need_resp = !linear && ((exc == kHammer && k2G > 0.f) || (exc == kBow && FB > 0.f));
 
@@ -768,7 +781,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
         }
       } else if (exc == kBow && FB > 0.f) {
         const float b = (node_interp<MU>(AC, en, ew, n_u) + 2.f * node_interp<MU>(DU, en, ew, n_u)) / (2.f * kk) -
-                        bow_v;
+                        bv;
         const float c = 0.5f * kk * FB * node_interp<MU>(XP, en, ew, n_u);
         const float phi = bow_phi(b, c, bow_a, bow_eps, bow_w);
         vrec = !(c > 0.f) ? b : (fabsf(b) <= c ? 0.f : b - c * phi);

@@ -141,8 +141,11 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
     }
   }
   const bool forced = exc != kPluck;
-  const int en = Dp->e_node;
-  const float ew = Dp->e_w, js = Dp->jscale;
+  int en = Dp->e_node;              // excitation point (a bow envelope moves it per step)
+  float ew = Dp->e_w;
+  const float js = Dp->jscale;
+  const int benv = exc == kBow ? Dp->bow_env_n : 0;
+  float bv = Dp->bow_v;             // the step's bow velocity
   auto load_J = [&](float* E) {      // E[i] = J_i for the lane's rows
     for (int r = 0; r < m_u; ++r) {
       const int i = ub + r;
@@ -221,7 +224,19 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         eta = uh - interp2(U, en, ew);
         if (eta > 0.f) k2G = Dp->ham_k2w * powf(eta, Dp->ham_expo);
       } else if (exc == kBow) {
-        FB = (n < Dp->bow_release_n) ? Dp->bow_F : 0.f;
+        float bf = Dp->bow_F;
+        if (benv > 0) {
+          const int en0 = en;
+          const float ew0 = ew;
+          bow_env_eval(Dp, n, bv, bf, en, ew);
+          if (linear && (en != en0 || ew != ew0)) {   // the fixed-matrix response A^-1 J follows x_B
+            __syncwarp();                             // the last step's reads of XP are done
+            load_J(XP);
+            tri_solve(SUB, INV, CP, FF, GG, XP, m_u, lane, rdu);
+            __syncwarp();
+          }
+        }
+        FB = (n < Dp->bow_release_n) ? bf : 0.f;
       }
       const bool need_resp = !linear && ((exc == kHammer && k2G > 0.f) || (exc == kBow && FB > 0.f));
 
@@ -379,7 +394,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         }
       } else if (exc == kBow && FB > 0.f) {
         const float k = Dp->k;
-        const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) / (2.f * k) - Dp->bow_v;
+        const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) / (2.f * k) - bv;
         const float c = 0.5f * k * FB * interp2(XP, en, ew);
         const float phi = bow_phi(b, c, Dp->bow_a, Dp->bow_eps, bow_w);
         vrec = !(c > 0.f) ? b : (fabsf(b) <= c ? 0.f : b - c * phi);

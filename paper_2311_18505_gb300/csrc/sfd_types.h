@@ -73,6 +73,13 @@ struct Desc {
   double mod_phase0;      // vibrato: phase / (2 pi)
   float mod_depth2;       // vibrato: 2 c / 1200
   float lam2_lo;          // lam2 + lam2_lo: wave coefficient to ~1e-15 (see fill_desc)
+  // time-varying bow controls (Sec. 3.3.1): bow_env_n breakpoints (0: the
+  // constant bow_v, bow_F, e_node / e_w), at steps bow_env_t (t fs) with
+  // v_B / L, F_B / (rho A L^2) and x_B; linear between, held outside
+  int32_t bow_env_n;
+  int32_t pad_env_;
+  double bow_env_t[16];
+  float bow_env_v[16], bow_env_f[16], bow_env_x[16];
   // state (device pointers into the string's pool block)
   float* u;               // u^n            [n_u]
   float* du;              // u^n - u^{n-1}  [n_u]

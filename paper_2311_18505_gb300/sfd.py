@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
         "sfd_excite_pluck": (i32, [vp, dbl, dbl]),
         "sfd_excite_hammer": (i32, [vp, dbl, dbl, dbl, dbl, dbl]),
         "sfd_excite_bow": (i32, [vp, dbl, dbl, dbl, dbl, dbl, dbl]),
+        "sfd_bow_envelope": (i32, [vp, i32, P(dbl), P(dbl), P(dbl), P(dbl)]),
         "sfd_set_modulation": (i32, [vp, i32, dbl, dbl, dbl, dbl]),
         "sfd_synthesize": (i32, [vp, i64, vp, i32]),
         "sfd_string_position": (i32, [vp, P(i64), P(i64)]),
@@ -219,6 +220,24 @@ def sfd_excite_hammer(s: int, mass_kg: float, vel_mps: float, pos: float, omega_
 def sfd_excite_bow(s: int, vel_mps: float, force_n: float, pos: float, a_s_per_m: float = 100.0,
                    eps: float = 0.1, release_time_s: float = -1.0) -> None:
     _check(lib().sfd_excite_bow(s, vel_mps, force_n, pos, a_s_per_m, eps, release_time_s))
+
+
+def sfd_bow_envelope(s: int, t_s, vel_mps=None, force_n=None, pos=None) -> None:
+    """Breakpoint envelopes of the bow velocity, force and position (None:
+    that control stays at its sfd_excite_bow value)."""
+    t = np.ascontiguousarray(t_s, dtype=np.float64)
+
+    def arr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == t.shape
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    v, f, x = arr(vel_mps), arr(force_n), arr(pos)
+    keep = (t, vel_mps, force_n, pos)   # the arrays outlive the call
+    _check(lib().sfd_bow_envelope(s, len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), v, f, x))
+    del keep
 
 
 def sfd_set_modulation(s: int, kind: int, rate_hz: float = 0.0, depth: float = 0.0, phase_rad: float = 0.0,
@@ -376,6 +395,8 @@ def sfd_last_error() -> str:
 
 
 def excitation_from_dict(ex: dict) -> sfd_excitation:
+    if ex.get("envelope"):
+        raise ValueError("bow envelopes apply to strings (string_from_dict), not to tapes or server requests")
     e = sfd_excitation()
     e.pos = ex["pos"]
     if ex["kind"] == "pluck":
@@ -537,6 +558,9 @@ def string_from_dict(ctx: int, d: dict) -> int:
         else:
             sfd_excite_bow(s, ex["vel"], ex["force"], ex["pos"], ex.get("a", 100.0), ex.get("eps", 0.1),
                            ex.get("release", -1.0))
+            env = ex.get("envelope")
+            if env:   # breakpoint times [s]; an absent key keeps that control constant
+                sfd_bow_envelope(s, env["t"], env.get("vel"), env.get("force"), env.get("pos"))
         mod = d.get("modulation", {"kind": "none"})
         if mod.get("kind") == "vibrato":
             sfd_set_modulation(s, SFD_MOD_VIBRATO, mod["rate"], mod["depth"], mod.get("phase", 0.0), 0.0)
