@@ -75,6 +75,11 @@ class Distribution:
     bow_a: tuple = (20.0, 200.0)
     bow_eps: tuple = (0.05, 0.3)
     bow_release: tuple = (0.5, 1.5)      # release time as a fraction of the note; >= 1: held
+    # time-varying bow controls (Sec. 3.3.1): with this probability a bowed
+    # item's v_B, F_B and x_B are envelopes through bow_env_points values
+    # drawn from the ranges above, evenly spaced over the note, linear between
+    p_bow_envelope: float = 0.0
+    bow_env_points: int = 4
     # f0 modulation: probabilities of a vibrato and of a glissando
     p_vibrato: float = 0.25
     p_gliss: float = 0.25
@@ -119,6 +124,15 @@ def draw(dist: Distribution, seed: int, index: int, attempt: int = 0) -> dict:
         ex = {"kind": "bow", "vel": _u(rng, dist.bow_vel), "force": _u(rng, dist.bow_force),
               "pos": _u(rng, dist.bow_pos), "a": _u(rng, dist.bow_a), "eps": _u(rng, dist.bow_eps),
               "release": rel * dist.seconds if rel < 1.0 else -1.0}
+        if dist.p_bow_envelope > 0.0:
+            # a stream of its own, so the other draws stay those of p_bow_envelope = 0
+            erng = np.random.Generator(np.random.PCG64([int(seed), int(index), int(attempt), 1]))
+            if float(erng.uniform()) < dist.p_bow_envelope:
+                m = min(16, max(2, int(dist.bow_env_points)))
+                ex["envelope"] = {"t": [dist.seconds * j / (m - 1) for j in range(m)],
+                                  "vel": [_u(erng, dist.bow_vel) for _ in range(m)],
+                                  "force": [_u(erng, dist.bow_force) for _ in range(m)],
+                                  "pos": [_u(erng, dist.bow_pos) for _ in range(m)]}
     else:
         raise ValueError(f"unknown excitation kind {kind!r}")
     r = float(rng.uniform())
@@ -364,12 +378,15 @@ def main(argv=None) -> None:
     ap.add_argument("--kinds", default="pluck,hammer,bow")
     ap.add_argument("--f0", type=float, nargs=2, default=(40.0, 1000.0))
     ap.add_argument("--no-modulation", action="store_true")
+    ap.add_argument("--p-bow-envelope", type=float, default=0.0,
+                    help="probability that a bowed item's velocity, force and position vary in time")
     ap.add_argument("--device", type=int, default=None)
     args = ap.parse_args(argv)
     dist = Distribution(seconds=args.seconds, fs=args.fs, output=args.output,
                         kinds=tuple(args.kinds.split(",")), f0=tuple(args.f0))
     if args.no_modulation:
         dist.p_vibrato = dist.p_gliss = 0.0
+    dist.p_bow_envelope = args.p_bow_envelope
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     device = args.device if args.device is not None else int(os.environ.get("LOCAL_RANK", "0"))

@@ -69,6 +69,31 @@ def test_draws_stay_in_their_ranges():
     assert abs(np.log(np.median(f0)) - 0.5 * np.log(40.0 * 1000.0)) < 0.15
 
 
+def test_bow_envelopes_are_drawn_on_their_own_stream():
+    """With p_bow_envelope > 0 bowed items get velocity, force and position
+    envelopes (Sec. 3.3.1) spanning the note, in the bow ranges; every other
+    parameter of every item is the draw of p_bow_envelope = 0."""
+    plain = D.Distribution()
+    env = D.Distribution(p_bow_envelope=0.5, bow_env_points=5)
+    n_env = n_bow = 0
+    for i in range(600):
+        a, b = D.draw(plain, 3, i), D.draw(env, 3, i)
+        eb = dict(b["excitation"])
+        e = eb.pop("envelope", None)
+        assert dict(b, excitation=eb) == a
+        if a["excitation"]["kind"] != "bow":
+            assert e is None
+            continue
+        n_bow += 1
+        if e is None:
+            continue
+        n_env += 1
+        assert e["t"] == [0.0, 0.25, 0.5, 0.75, 1.0]
+        for key, rng in (("vel", env.bow_vel), ("force", env.bow_force), ("pos", env.bow_pos)):
+            assert len(e[key]) == 5 and all(rng[0] <= v <= rng[1] for v in e[key]), key
+    assert abs(n_env / n_bow - 0.5) < 0.1
+
+
 def test_shard_plan_partitions_the_items():
     assert D.shard_ranges(0, 4) == []
     assert D.shard_ranges(10, 4) == [(0, 4), (4, 8), (8, 10)]

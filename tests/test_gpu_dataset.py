@@ -79,3 +79,27 @@ def test_items_match_the_oracle(dataset):
                 continue
             e = np.linalg.norm(audio[m["index"], c] - ref) / np.linalg.norm(ref)
             assert e <= 1e-4 or e <= 3 * fp32_floor(d, d["n_samples"]), (m["index"], ch, e)
+
+
+def test_bow_envelope_items(sfd, renderer, tmp_path):
+    """Bowed items with time-varying velocity, force and position: each row
+    is the string's own synthesis, and its first 150 samples (the window
+    before FP32 and FP64 may take a stick/slip switch a step apart) match
+    the oracle to 1e-3."""
+    dist = D.Distribution(seconds=0.0125, kinds=("bow",), p_bow_envelope=1.0, p_vibrato=0.0, p_gliss=0.0)
+    out = str(tmp_path / "bow")
+    D.generate(out, 6, dist, seed=5, shard_size=4, render=renderer)
+    assert D.merge_metadata(out) == 6
+    audio, _, status = D.load(out)
+    assert not status.any()
+    meta = [json.loads(l) for l in open(os.path.join(out, "metadata.jsonl"))]
+    for i, m in enumerate(meta):
+        d = m["params"]
+        assert "envelope" in d["excitation"]
+        s = sfd.string_from_dict(renderer.ctx, d)
+        try:
+            assert np.array_equal(audio[i], sfd.sfd_synthesize(s, d["n_samples"])), i
+        finally:
+            sfd.sfd_string_destroy(s)
+        ref = oracle.run(d)
+        assert np.linalg.norm(audio[i, :150] - ref[:150]) <= 1e-3 * np.linalg.norm(ref[:150]), i
