@@ -361,6 +361,13 @@ sfd_status sfd_server_create(sfd_ctx* ctx, int32_t chunk_samples, int32_t max_li
 /* Validates and queues a request (host only).  SFD_EINVAL for invalid
  * parameters, SFD_ENOMEM for a note whose state can never fit the pool. */
 sfd_status sfd_server_submit(sfd_server* sv, const sfd_request* req);
+/* The same for a bowed request whose velocity, force and position vary in
+ * time (Sec. 3.3.1): the breakpoints as in sfd_bow_envelope, copied before
+ * the call returns (the caller keeps ownership of the arrays).  SFD_EINVAL
+ * also when the request is not bowed or n_points is outside 1..16. */
+sfd_status sfd_server_submit_bow_envelope(sfd_server* sv, const sfd_request* req, int32_t n_points,
+                                          const double* t_s, const double* vel_mps, const double* force_n,
+                                          const double* pos);
 /* One admission + launch + delivery round (see above).  *chunks points to
  * *n_chunks records owned by the server, valid until the next pump. */
 sfd_status sfd_server_pump(sfd_server* sv, const sfd_chunk** chunks, int32_t* n_chunks);

@@ -491,6 +491,8 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
     s->h.bow_v = static_cast<float>(ex.vel_mps / q.length_m);
     s->h.bow_a = static_cast<float>(ex.a_s_per_m * q.length_m);
     s->h.bow_eps = static_cast<float>(ex.eps);
+    s->h.bow_env_n = 0;
+    s->bow_pos = pos;
     s->h.bow_release_n = INT64_MAX;
     if (ex.release_time_s >= 0) {
       // first step n with n k >= release
@@ -956,10 +958,12 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   return upload_initial(s);
 }
 
-sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, const double* vel_mps,
-                            const double* force_n, const double* pos) {
-  if (!s || !t_s) return fail(SFD_EINVAL, "NULL argument");
-  if (s->started) return fail(SFD_ESTATE, "set the bow envelope before synthesizing");
+// Breakpoint envelopes of the bow controls into the host descriptor (times
+// in steps, velocity and force in normalised units); NULL arrays keep the
+// constant controls.
+sfd_status apply_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, const double* vel_mps,
+                              const double* force_n, const double* pos) {
+  if (!t_s) return fail(SFD_EINVAL, "NULL breakpoint times");
   if (s->exc != kBow) return fail(SFD_EINVAL, "the string is not bowed (call sfd_excite_bow first)");
   if (n_points < 1 || n_points > 16) return fail(SFD_EINVAL, "1 to 16 breakpoints");
   const sfd_string_params& p = s->p;
@@ -980,7 +984,16 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
     D.bow_env_x[j] = pos ? static_cast<float>(pos[j]) : static_cast<float>(x0);
   }
   D.bow_env_n = n_points;
-  sfd_status rc = set_device(s->ctx);
+  return SFD_OK;
+}
+
+sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, const double* vel_mps,
+                            const double* force_n, const double* pos) {
+  if (!s) return fail(SFD_EINVAL, "NULL argument");
+  if (s->started) return fail(SFD_ESTATE, "set the bow envelope before synthesizing");
+  sfd_status rc = apply_bow_envelope(s, n_points, t_s, vel_mps, force_n, pos);
+  if (rc) return rc;
+  rc = set_device(s->ctx);
   if (rc) return rc;
   SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
   SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));

@@ -155,13 +155,15 @@ sfd_status sfd_server_create(sfd_ctx* c, int32_t chunk_samples, int32_t max_live
   return SFD_OK;
 }
 
-sfd_status sfd_server_submit(sfd_server* sv, const sfd_request* r) {
+static sfd_status submit_note(sfd_server* sv, const sfd_request* r, int32_t env_n, const double* env_t,
+                              const double* env_v, const double* env_f, const double* env_x) {
   if (!sv || !r) return fail(SFD_EINVAL, "NULL argument");
   if (r->n_samples <= 0) return fail(SFD_EINVAL, "n_samples must be > 0");
   sfd_string* s = new (std::nothrow) sfd_string();
   if (!s) return fail(SFD_ENOMEM, "host allocation failed");
   sfd_status rc = init_host_string(r->params, s);
   if (rc == SFD_OK) rc = apply_excitation(s, r->exc);
+  if (rc == SFD_OK && env_n > 0) rc = apply_bow_envelope(s, env_n, env_t, env_v, env_f, env_x);
   if (rc == SFD_OK) rc = apply_modulation(s, r->mod_kind, r->mod_rate_hz, r->mod_depth, r->mod_phase_rad,
                                           r->mod_duration_s);
   if (rc == SFD_OK) {
@@ -188,6 +190,16 @@ sfd_status sfd_server_submit(sfd_server* sv, const sfd_request* r) {
   sv->queue.push_back(nt);
   sv->st.submitted++;
   return SFD_OK;
+}
+
+sfd_status sfd_server_submit(sfd_server* sv, const sfd_request* r) {
+  return submit_note(sv, r, 0, nullptr, nullptr, nullptr, nullptr);
+}
+
+sfd_status sfd_server_submit_bow_envelope(sfd_server* sv, const sfd_request* r, int32_t n_points, const double* t_s,
+                                          const double* vel_mps, const double* force_n, const double* pos) {
+  if (n_points <= 0) return fail(SFD_EINVAL, "1 to 16 breakpoints");
+  return submit_note(sv, r, n_points, t_s, vel_mps, force_n, pos);
 }
 
 sfd_status sfd_server_pump(sfd_server* sv, const sfd_chunk** chunks, int32_t* n_chunks) {

@@ -137,6 +137,7 @@ def lib() -> ctypes.CDLL:
         "sfd_synthesize_noalloc": (i32, [ctypes.c_int, vp, P(sfd_string_params), P(sfd_excitation), i64, vp]),
         "sfd_server_create": (i32, [vp, i32, i32, P(vp)]),
         "sfd_server_submit": (i32, [vp, P(sfd_request)]),
+        "sfd_server_submit_bow_envelope": (i32, [vp, P(sfd_request), i32, P(dbl), P(dbl), P(dbl), P(dbl)]),
         "sfd_server_pump": (i32, [vp, P(P(sfd_chunk)), P(i32)]),
         "sfd_server_clock": (dbl, [vp]),
         "sfd_server_stats_get": (i32, [vp, P(sfd_server_stats)]),
@@ -225,19 +226,8 @@ def sfd_excite_bow(s: int, vel_mps: float, force_n: float, pos: float, a_s_per_m
 def sfd_bow_envelope(s: int, t_s, vel_mps=None, force_n=None, pos=None) -> None:
     """Breakpoint envelopes of the bow velocity, force and position (None:
     that control stays at its sfd_excite_bow value)."""
-    t = np.ascontiguousarray(t_s, dtype=np.float64)
-
-    def arr(a):
-        if a is None:
-            return None
-        a = np.ascontiguousarray(a, dtype=np.float64)
-        assert a.shape == t.shape
-        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-
-    v, f, x = arr(vel_mps), arr(force_n), arr(pos)
-    keep = (t, vel_mps, force_n, pos)   # the arrays outlive the call
-    _check(lib().sfd_bow_envelope(s, len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), v, f, x))
-    del keep
+    t, v, f, x = _env_arrays(t_s, vel_mps, force_n, pos)
+    _check(lib().sfd_bow_envelope(s, len(t), _dptr(t), _dptr(v), _dptr(f), _dptr(x)))
 
 
 def sfd_set_modulation(s: int, kind: int, rate_hz: float = 0.0, depth: float = 0.0, phase_rad: float = 0.0,
@@ -396,7 +386,7 @@ def sfd_last_error() -> str:
 
 def excitation_from_dict(ex: dict) -> sfd_excitation:
     if ex.get("envelope"):
-        raise ValueError("bow envelopes apply to strings (string_from_dict), not to tapes or server requests")
+        raise ValueError("bow envelopes apply to strings and server requests, not to tapes")
     e = sfd_excitation()
     e.pos = ex["pos"]
     if ex["kind"] == "pluck":
@@ -426,8 +416,33 @@ def sfd_server_create(ctx: int, chunk_samples: int = 1024, max_live: int = 4096)
     return out.value
 
 
+def _env_arrays(t_s, vel_mps, force_n, pos):
+    """Breakpoint arrays as contiguous float64 (None for an absent control)."""
+    t = np.ascontiguousarray(t_s, dtype=np.float64)
+    out = []
+    for a in (vel_mps, force_n, pos):
+        if a is not None:
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            if a.shape != t.shape:
+                raise ValueError("every envelope array needs one value per breakpoint time")
+        out.append(a)
+    return [t] + out
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
 def sfd_server_submit(sv: int, req: sfd_request) -> None:
-    _check(lib().sfd_server_submit(sv, ctypes.byref(req)))
+    """Queue a request; one made by request_from_dict from a bowed string
+    with an "envelope" carries it (sfd_server_submit_bow_envelope)."""
+    env = getattr(req, "bow_envelope", None)
+    if env is None:
+        _check(lib().sfd_server_submit(sv, ctypes.byref(req)))
+        return
+    t, v, f, x = _env_arrays(env["t"], env.get("vel"), env.get("force"), env.get("pos"))
+    _check(lib().sfd_server_submit_bow_envelope(sv, ctypes.byref(req), len(t), _dptr(t), _dptr(v), _dptr(f),
+                                                _dptr(x)))
 
 
 def sfd_server_pump(sv: int, copy: bool = True):
@@ -507,7 +522,11 @@ def sfd_tape_destroy(tape: int) -> None:
 def request_from_dict(d: dict, tag: int, n_samples: int | None = None, arrival_s: float = -1.0) -> sfd_request:
     r = sfd_request()
     r.params = params_from_dict(d)
-    r.exc = excitation_from_dict(d["excitation"])
+    ex = dict(d["excitation"])
+    env = ex.pop("envelope", None)
+    r.exc = excitation_from_dict(ex)
+    if env:
+        r.bow_envelope = env   # sent by sfd_server_submit
     mod = d.get("modulation", {"kind": "none"})
     if mod.get("kind") == "vibrato":
         r.mod_kind, r.mod_rate_hz, r.mod_depth, r.mod_phase_rad = SFD_MOD_VIBRATO, mod["rate"], mod["depth"], \

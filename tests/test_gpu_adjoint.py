@@ -364,7 +364,7 @@ def test_autograd_function_and_a_descent_step(sfd, ctx):
         step = -1e-3 * theta * torch.sign(theta.grad)
         y2 = G.synthesize(theta + step, base, N_SHORT, ctx)
         loss2 = ((y2.double() - tgt) ** 2).sum()
-    assert float(loss2) < float(loss)
+    assert loss2.item() < loss.detach().item()
 
 
 def test_full_differentiation_workload_against_the_oracle(sfd, ctx):

@@ -128,5 +128,6 @@ def test_envelope_errors(sfd, ctx):
         assert e.value.code == sfd.SFD_ESTATE           # already started
     finally:
         sfd.sfd_string_destroy(s)
+    # tapes take no envelope: the binding refuses one
     with pytest.raises(ValueError):
-        sfd.request_from_dict(dict(bowed, excitation=dict(BOW, envelope=ENV)), 0)
+        sfd.excitation_from_dict(dict(BOW, envelope=ENV))

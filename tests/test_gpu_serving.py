@@ -201,3 +201,31 @@ def test_longitudinal_notes_served(sfd):
     finally:
         sfd.sfd_server_destroy(sv)
         sfd.sfd_ctx_destroy(ctx)
+
+
+def test_bow_envelope_notes_served(sfd):
+    """Bowed notes with time-varying velocity, force and position (Sec.
+    3.3.1), served beside plain notes, equal the same notes alone; a
+    non-bowed request with an envelope is refused."""
+    ctx = sfd.sfd_ctx_create(0, None, 128 << 20)
+    sv = sfd.sfd_server_create(ctx, CHUNK, 32)
+    try:
+        notes = short_notes(0.004, seed=19, lo=1500, hi=4000)[:8]
+        env = {"t": [0.0, 0.01, 0.03], "vel": [0.05, 0.4, 0.2], "force": [0.3, 2.0, 0.8], "pos": [0.12, 0.3, 0.2]}
+        bow = {"kind": "bow", "vel": 0.2, "force": 1.0, "pos": 0.17, "a": 100.0, "eps": 0.1, "release": -1.0}
+        notes = [dict(d, excitation=dict(bow, envelope=env)) if i % 2 else d for i, d in enumerate(notes)]
+        for tag, d in enumerate(notes):
+            sfd.sfd_server_submit(sv, sfd.request_from_dict(d, tag))
+        pluck = dict(notes[0], excitation={"kind": "pluck", "amp": 1e-3, "pos": 0.3, "envelope": env})
+        with pytest.raises(sfd.SfdError) as e:
+            sfd.sfd_server_submit(sv, sfd.request_from_dict(pluck, 99))
+        assert e.value.code == sfd.SFD_EINVAL
+        audio, stats_log, finished = {}, [], {}
+        drain(sfd, sv, audio, stats_log, finished)
+        assert sorted(finished) == list(range(len(notes)))
+        for tag, d in enumerate(notes):
+            assert finished[tag] == sfd.SFD_OK
+            assert np.array_equal(np.concatenate(audio[tag]), alone(sfd, ctx, d)), tag
+    finally:
+        sfd.sfd_server_destroy(sv)
+        sfd.sfd_ctx_destroy(ctx)
