@@ -384,6 +384,53 @@ def test_bow_power_budget_and_friction():
     assert stick > 10 and slip > 10
 
 
+def test_bow_envelope_power_budget():
+    """Time-varying bow (Sec. 3.3.1, reading A20), from the states alone: a
+    lossless bowed string whose v_B, F_B and x_B move changes its energy
+    over each step n -> n+1 by exactly k F I_n(dt.u), where I_n interpolates
+    linearly at x_B(t_n) and the controls are linear in time at t_n = n k.
+    Slipping steps obey F = -F_B(t_n) phi(I_n(dt.u) - v_B(t_n)); sticking
+    steps have I_n(dt.u) = v_B(t_n) and |F| <= F_B(t_n)."""
+    env = {"t": [0.0, 0.004, 0.01, 0.02], "vel": [0.05, 0.4, 0.15, 0.3], "force": [0.2, 2.0, 1.0, 0.6],
+           "pos": [0.12, 0.31, 0.2, 0.44]}
+    ex = {"kind": "bow", "vel": 0.2, "force": 1.0, "pos": 0.17, "a": 100.0, "eps": 0.1, "release": -1.0,
+          "envelope": env}
+    d = W.make(alpha=2.0, sigma0=0.0, sigma1=0.0, excitation=ex)
+    s = _fresh(d)
+    n0 = s.time_level
+    g = Grid(s.n_t, s.n_l, d)
+    st = _states(s, 1100)
+    k, L = g.k, d["length"]
+
+    def interp(u, x):
+        pos = x * s.n_t
+        l = min(int(math.floor(pos)), s.n_t - 1)
+        w = pos - l
+        node = lambda j: u[j - 1] if 1 <= j <= s.n_t - 1 else 0.0
+        return (1.0 - w) * node(l) + w * node(l + 1)
+
+    stick = slip = 0
+    for i in range(1, len(st) - 1):
+        t = (n0 + i) * k                           # u^n = st[i][1], step n -> n+1
+        vB = np.interp(t, env["t"], env["vel"]) / L
+        FB = np.interp(t, env["t"], env["force"]) / (d["rho_a"] * L * L)
+        xB = np.interp(t, env["t"], env["pos"])
+        vI = (interp(st[i + 1][1], xB) - interp(st[i - 1][1], xB)) / (2.0 * k)
+        v = vI - vB
+        Hm = energy(g, st[i - 1][1], st[i][1], st[i - 1][3], st[i][3])
+        Hp = energy(g, st[i][1], st[i + 1][1], st[i][3], st[i + 1][3])
+        tol = 1e-10 * abs(Hp) + 1e-18
+        if abs(v) <= 1e-9 * abs(vB):
+            stick += 1
+            assert abs(Hp - Hm) <= k * FB * abs(vI) * (1 + 1e-9) + tol
+        else:
+            slip += 1
+            phi = math.copysign(ex["eps"] + (1 - ex["eps"]) * math.exp(-ex["a"] * L * abs(v)), v)
+            assert abs((Hp - Hm) - k * (-FB * phi) * vI) <= tol
+    assert stick > 50 and slip > 50
+    assert s.time_level == n0 + len(st) - 1
+
+
 # ---------------------------------------------------------- brute force
 
 EXCS = [
