@@ -143,6 +143,12 @@ struct sfd_ctx {
   int* d_counter = nullptr;                // kClasses work-queue counters
   int last_launches = 0;
   uint64_t h2d_bytes = 0, d2h_bytes = 0;   // all host<->device copies made
+  // pinned staging of strings' initial blocks (flush_strings); the event
+  // marks the last flush's copies, after which the buffer may be rewritten
+  char* stage = nullptr;
+  size_t stage_cap = 0;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
 };
 
 struct sfd_string {
@@ -155,6 +161,7 @@ struct sfd_string {
   Desc* d_desc = nullptr;
   Scalars* d_sc = nullptr;
   bool started = false;     // first synthesize done
+  mutable bool dirty = false;   // host image newer than the device block (flush_strings)
   int batch_refs = 0;
   // excitation (kept to rebuild the initial state)
   int exc = kPluck;
@@ -402,7 +409,51 @@ void write_image(const sfd_string* s, char* img) {
   }
 }
 
-// Upload the descriptor and the initial state (one copy of the block image).
+// A string's device block (descriptor, scalars, initial state) is written
+// on first use: creation, excitation, modulation and envelope calls only
+// update the host descriptor and mark the string, and every call that runs
+// or reads a string first flushes the marked ones, each with one
+// asynchronous copy from the context's pinned staging buffer, ordered on the
+// stream before the call's own work (no synchronisation per string).
+void stage_initial(sfd_string* s) { s->dirty = true; }
+
+sfd_status flush_strings(sfd_ctx* c, const sfd_string* const* ss, size_t n) {
+  constexpr size_t kA = 256;
+  size_t bytes = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (ss[i]->dirty) bytes += (block_bytes(ss[i]->h) + kA - 1) / kA * kA;
+  if (bytes == 0) return SFD_OK;
+  if (c->stage_pending) {   // the previous flush's copies still read the buffer
+    SFD_CUDA(cudaEventSynchronize(c->stage_done));
+    c->stage_pending = false;
+  }
+  if (bytes > c->stage_cap) {
+    if (c->stage) cudaFreeHost(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    const size_t cap = std::max(bytes, size_t{1} << 20);
+    SFD_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->stage), cap, cudaHostAllocDefault));
+    c->stage_cap = cap;
+  }
+  if (!c->stage_done) SFD_CUDA(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
+  size_t off = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const sfd_string* s = ss[i];
+    if (!s->dirty) continue;
+    const size_t bb = block_bytes(s->h);
+    write_image(s, c->stage + off);
+    SFD_CUDA(h2d(c, s->block, c->stage + off, bb));
+    s->dirty = false;
+    off += (bb + kA - 1) / kA * kA;
+  }
+  SFD_CUDA(cudaEventRecord(c->stage_done, c->stream));
+  c->stage_pending = true;
+  return SFD_OK;
+}
+
+sfd_status flush_string(const sfd_string* s) { return flush_strings(s->ctx, &s, 1); }
+
+// Upload the descriptor and the initial state now (one copy of the block image).
 sfd_status upload_initial(sfd_string* s) {
   std::vector<char> img(block_bytes(s->h));
   write_image(s, img.data());
@@ -787,6 +838,8 @@ void sfd_ctx_destroy(sfd_ctx* c) {
     if (c->t1[k]) cudaEventDestroy(c->t1[k]);
   }
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->stage_done) cudaEventDestroy(c->stage_done);
+  if (c->stage) cudaFreeHost(c->stage);
   c->pool.release();
   if (c->d_jobs) cudaFree(c->d_jobs);
   if (c->d_counter) cudaFree(c->d_counter);
@@ -875,11 +928,7 @@ sfd_status sfd_string_create(sfd_ctx* c, const sfd_string_params* p, sfd_string*
     return fail(SFD_ENOMEM, "device pool exhausted (%zu of %zu bytes used)", c->pool.used(), c->pool.size());
   }
   carve(s);
-  if ((rc = upload_initial(s))) {
-    c->pool.dealloc(s->block);
-    delete s;
-    return rc;
-  }
+  stage_initial(s);
   *out = s;
   return SFD_OK;
 }
@@ -903,7 +952,8 @@ sfd_status sfd_excite_pluck(sfd_string* s, double amp_m, double pos) {
   fill_desc(s);
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
-  return upload_initial(s);
+  stage_initial(s);
+  return SFD_OK;
 }
 
 sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, double pos, double omega_h,
@@ -923,7 +973,8 @@ sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, doub
   s->hammer_uh1 = (vel_mps / p.length_m) * s->k;
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
-  return upload_initial(s);
+  stage_initial(s);
+  return SFD_OK;
 }
 
 sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double pos, double a_s_per_m, double eps,
@@ -955,7 +1006,8 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   }
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
-  return upload_initial(s);
+  stage_initial(s);
+  return SFD_OK;
 }
 
 // Breakpoint envelopes of the bow controls into the host descriptor (times
@@ -993,10 +1045,7 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
   if (s->started) return fail(SFD_ESTATE, "set the bow envelope before synthesizing");
   sfd_status rc = apply_bow_envelope(s, n_points, t_s, vel_mps, force_n, pos);
   if (rc) return rc;
-  rc = set_device(s->ctx);
-  if (rc) return rc;
-  SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
-  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  stage_initial(s);
   return SFD_OK;
 }
 
@@ -1006,10 +1055,7 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
   if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
   sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
   if (rc) return rc;
-  rc = set_device(s->ctx);
-  if (rc) return rc;
-  SFD_CUDA(h2d(s->ctx, s->d_desc, &s->h, sizeof(Desc)));
-  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  stage_initial(s);
   return SFD_OK;
 }
 
@@ -1020,6 +1066,7 @@ sfd_status sfd_synthesize(sfd_string* s, int64_t n_samples, float* out, int32_t 
   sfd_ctx* c = s->ctx;
   sfd_status rc = set_device(c);
   if (rc) return rc;
+  if ((rc = flush_string(s))) return rc;
   float* dout = out;
   char* tmp = nullptr;
   if (!out_on_device) {
@@ -1050,6 +1097,7 @@ sfd_status sfd_string_position(const sfd_string* s, int64_t* time_level, int64_t
   Scalars sc{};
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
+  if ((rc = flush_string(s))) return rc;
   if ((rc = read_status(s, &sc))) return rc;
   if (time_level) *time_level = sc.n;
   if (next_sample) *next_sample = sc.next_out;
@@ -1060,6 +1108,7 @@ sfd_status sfd_string_state(const sfd_string* s, float* u_prev, float* u, float*
   if (!s) return fail(SFD_EINVAL, "string is NULL");
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
+  if ((rc = flush_string(s))) return rc;
   const Desc& D = s->h;
   const int nz_full = s->n_l - 1;
   std::vector<float> hu(D.n_u), hdu(D.n_u), hz(std::max(D.n_z, 1)), hdz(std::max(D.n_z, 1));
@@ -1088,6 +1137,7 @@ sfd_status sfd_string_stats(const sfd_string* s, int32_t* status, int32_t* max_s
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
   Scalars sc{};
+  if ((rc = flush_string(s))) return rc;
   if ((rc = read_status(s, &sc))) return rc;
   if (status) *status = status_code(sc);
   if (max_sweeps) *max_sweeps = sc.max_sweeps;
@@ -1108,10 +1158,13 @@ sfd_status sfd_string_destroy(sfd_string* s) {
 sfd_status sfd_batch_create(sfd_ctx* c, int32_t n, sfd_string* const* strings, sfd_batch** out) {
   if (!c || !out || (n > 0 && !strings) || n < 0) return fail(SFD_EINVAL, "bad batch arguments");
   *out = nullptr;
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n; ++i)
     if (!strings[i] || strings[i]->ctx != c) return fail(SFD_EINVAL, "string %d is NULL or from another ctx", i);
-    for (int j = 0; j < i; ++j)
-      if (strings[j] == strings[i]) return fail(SFD_EINVAL, "string %d appears twice", i);
+  {
+    std::vector<sfd_string*> sorted(strings, strings + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(SFD_EINVAL, "a string appears twice in the batch");
   }
   sfd_batch* b = new (std::nothrow) sfd_batch();
   if (!b) return fail(SFD_ENOMEM, "host allocation failed");
@@ -1127,6 +1180,7 @@ static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_d
   sfd_ctx* c = b->ctx;
   sfd_status rc = set_device(c);
   if (rc) return rc;
+  if ((rc = flush_strings(c, b->strings.data(), b->strings.size()))) return rc;
   std::vector<Job> jobs;
   std::vector<const sfd_string*> owners;
   for (size_t i = 0; i < b->strings.size(); ++i) {
@@ -1195,6 +1249,7 @@ sfd_status sfd_batch_prepare(sfd_batch* b, const int64_t* n_samples, float* out_
   sfd_ctx* c = b->ctx;
   sfd_status rc = set_device(c);
   if (rc) return rc;
+  if ((rc = flush_strings(c, b->strings.data(), b->strings.size()))) return rc;
   std::vector<Job> jobs;
   std::vector<const sfd_string*> owners;
   for (size_t i = 0; i < b->strings.size(); ++i) {
@@ -1225,10 +1280,17 @@ sfd_status sfd_batch_launch(sfd_batch* b) {
   sfd_ctx* c = b->ctx;
   sfd_status rc = set_device(c);
   if (rc) return rc;
-  for (auto* s : b->strings) s->started = true;
-  // per-class timing events cannot be read back from a graph: off while capturing
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SFD_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+  // a string excited or modulated since sfd_batch_prepare is uploaded now;
+  // a graph cannot hold that copy (the staging buffer is reused)
+  bool dirty = false;
+  for (auto* s : b->strings) dirty = dirty || s->dirty;
+  if (dirty && cap != cudaStreamCaptureStatusNone)
+    return fail(SFD_ESTATE, "a string changed after sfd_batch_prepare: prepare again before capturing");
+  if (dirty && (rc = flush_strings(c, b->strings.data(), b->strings.size()))) return rc;
+  for (auto* s : b->strings) s->started = true;
+  // per-class timing events cannot be read back from a graph: off while capturing
   const bool timing = c->timing;
   if (cap != cudaStreamCaptureStatusNone) c->timing = false;
   rc = issue_plan(c, *static_cast<Plan*>(b->plan), reinterpret_cast<const Job*>(b->d_jobs));
@@ -1269,6 +1331,7 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
   if (rc) return rc;
   const size_t n = b->strings.size();
   if (n == 0) return fail(SFD_EINVAL, "empty batch");
+  if ((rc = flush_strings(c, b->strings.data(), n))) return rc;   // the clones copy the device blocks
   char* dout = c->pool.alloc(sizeof(float) * probe_samples * n);
   if (!dout) return fail(SFD_ENOMEM, "device pool exhausted for the probe output");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
