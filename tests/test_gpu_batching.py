@@ -78,6 +78,37 @@ def test_graph_replay_equals_direct_chunks(sfd):
         sfd.sfd_ctx_destroy(ctx)
 
 
+def test_string_changed_after_prepare_is_uploaded_at_launch(sfd):
+    """A string excited again after sfd_batch_prepare (allowed until it first
+    runs) starts from its new initial state when sfd_batch_launch runs the
+    batch; every string equals its own synthesis alone."""
+    ctx = sfd.sfd_ctx_create(0, None, 128 << 20)
+    try:
+        strings = W.batch_mixed(6, seconds=0.05, seed=7)
+        n = 1000
+        ns = np.full(len(strings), n, np.int64)
+        offs = np.arange(len(strings), dtype=np.int64) * n
+        hs, b = make_batch(sfd, ctx, strings)
+        out = torch.zeros(len(strings) * n, device="cuda")
+        torch.cuda.synchronize()
+        sfd.sfd_batch_prepare(b, ns, out, offs)
+        assert strings[2]["excitation"]["kind"] == "hammer"
+        hit = {"kind": "hammer", "mass": 7e-3, "vel": 4.5, "pos": 0.41, "omega": 2500.0, "alpha": 2.2}
+        sfd.sfd_excite_hammer(hs[2], hit["mass"], hit["vel"], hit["pos"], hit["omega"], hit["alpha"])
+        sfd.sfd_batch_launch(b)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(len(strings), n)
+        free(sfd, hs, b)
+        for i, d in enumerate(strings):
+            s = sfd.string_from_dict(ctx, dict(d, excitation=hit) if i == 2 else d)
+            try:
+                assert np.array_equal(got[i], sfd.sfd_synthesize(s, n)), i
+            finally:
+                sfd.sfd_string_destroy(s)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
+
+
 def test_autotune_does_not_advance_strings(sfd):
     ctx = sfd.sfd_ctx_create(0, None, 256 << 20)
     try:
