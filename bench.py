@@ -387,11 +387,8 @@ def run_ours(args, ws, rank, local):
     e2e = None
     if not args.no_e2e:
         host_out = torch.empty(total, dtype=torch.float32).pin_memory()
-        h0, d0 = sfd.sfd_ctx_transfer_bytes(ctx)
-        barrier(ws)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+
+        def e2e_step():
             hs = [sfd.string_from_dict(ctx, d) for d in strings]
             b = sfd.sfd_batch_create(ctx, hs)
             sfd.lib().sfd_batch_synthesize_host(
@@ -400,6 +397,14 @@ def run_ours(args, ws, rank, local):
             sfd.sfd_batch_destroy(b)
             for h in hs:
                 sfd.sfd_string_destroy(h)
+
+        e2e_step()   # untimed: first touch of the output buffer and the staging
+        h0, d0 = sfd.sfd_ctx_transfer_bytes(ctx)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
         torch.cuda.synchronize(dev)
         dt = max_over_ranks(ws, time.perf_counter() - t0)
         h1, d1 = sfd.sfd_ctx_transfer_bytes(ctx)
@@ -810,7 +815,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--warp-groups", type=int, default=1, choices=[0, 1],
                     help="1: large-grid strings may take 2 or 4 warps (sfd_ctx_set_warp_pairs)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # oracle samples: the whole 256 x 2 s batch for the baseline (~17 s on 16
     # cores), half of it per step for the reference arm
