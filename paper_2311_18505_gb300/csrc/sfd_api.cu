@@ -437,17 +437,24 @@ sfd_status flush_strings(sfd_ctx* c, const sfd_string* const* ss, size_t n) {
   }
   if (!c->stage_done) SFD_CUDA(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
   size_t off = 0;
-  for (size_t i = 0; i < n; ++i) {
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
     const sfd_string* s = ss[i];
     if (!s->dirty) continue;
     const size_t bb = block_bytes(s->h);
     write_image(s, c->stage + off);
-    SFD_CUDA(h2d(c, s->block, c->stage + off, bb));
-    s->dirty = false;
+    e = h2d(c, s->block, c->stage + off, bb);
+    if (e == cudaSuccess) s->dirty = false;
     off += (bb + kA - 1) / kA * kA;
   }
-  SFD_CUDA(cudaEventRecord(c->stage_done, c->stream));
-  c->stage_pending = true;
+  // copies already enqueued read the buffer until this event, even after an error
+  const cudaError_t er = cudaEventRecord(c->stage_done, c->stream);
+  c->stage_pending = er == cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "upload of initial blocks");
+  if (er != cudaSuccess) {
+    cudaStreamSynchronize(c->stream);
+    return cuda_fail(er, "cudaEventRecord");
+  }
   return SFD_OK;
 }
 
