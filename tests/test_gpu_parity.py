@@ -2,9 +2,10 @@
 
 Bar (from the method's accuracy target): relative L2 error of the output
 waveform <= 1e-4 over the first 0.25 s, energy drift <= 1e-5 for the
-lossless scheme.  Bowed strings are compared over a short window only: a
-stick/slip switch taken one step apart in FP32 and FP64 makes the
-trajectories part, so beyond it only the invariants are checked."""
+lossless scheme.  Bowed strings are compared over a short window at 1e-3,
+and over 0.5 s at 1e-3 wherever the FP64 trajectory is itself stable under
+FP32-sized state noise; a bowed note near a bifurcation, which that noise
+moves into another periodic regime, is compared by its level."""
 
 import math
 
@@ -85,26 +86,52 @@ def test_bow_short_window(sfd, ctx, alpha):
     assert np.all(np.isfinite(y)) and np.max(np.abs(y)) < 10 * np.max(np.abs(ref)) + 1e-9
 
 
-def test_bowed_notes_keep_the_oracles_pitch_and_level(sfd, ctx):
-    """Bowed notes beyond the short window, by what every correct trajectory
-    shares with the oracle's: over 0.5 s, the second half's fundamental
-    (the spectral peak near f0) within 0.2 % and its RMS within 2 % of the
-    FP64 oracle's, for the first 12 bowed strings of the 256-string batch.
-    In the oracle a relative change of 1e-6 in the bow velocity moves
-    neither statistic beyond rounding on these strings."""
+def oracle_with_state_noise(d, n, eps, seed):
+    """The oracle's output with every level of u and zeta multiplied by
+    (1 + eps N(0, 1)) noise after each step: an FP64 trajectory perturbed
+    at the size of FP32 rounding."""
+    rng = np.random.default_rng(seed)
+    s = oracle.OracleString(d)
+    y = list(s.run(2))
+    for _ in range(2, n):
+        up, u, zp, z, _ = s.state()
+        s.set_state(up, u * (1 + eps * rng.standard_normal(u.shape)), zp,
+                    z * (1 + eps * rng.standard_normal(z.shape)) if len(z) else None)
+        y.extend(s.run(1))
+    return np.array(y)
+
+
+def test_bowed_notes_over_half_a_second(sfd, ctx):
+    """Bowed notes over 0.5 s, the first 8 bowed strings of the 256-string
+    batch.  Where the FP64 trajectory is stable under FP32-sized state noise
+    (1e-7 relative per step keeps the oracle within 1e-3), the GPU waveform
+    is within 1e-3 of the oracle over the whole note and the second half's
+    fundamental within 0.2 %.  Where that noise itself moves the note into
+    another periodic regime (a bowed string near a bifurcation), no FP32
+    run can follow the FP64 one; there the level is what every correct run
+    shares: the second half's RMS within 5 %.  Most of these strings are
+    stable (at least 6 of 8 required)."""
     from pitch import peak_frequency
     n = 24000
     strings = [dict(d, n_samples=n) for d in W.batch_mixed(256, seconds=2.0, seed=2)
-               if d["excitation"]["kind"] == "bow"][:12]
+               if d["excitation"]["kind"] == "bow"][:8]
     refs, _ = oracle.run_batch(strings)
+    stable = 0
     for i, (d, ref) in enumerate(zip(strings, refs)):
-        y = np.asarray(gpu_run(sfd, ctx, d), np.float64)[n // 2:]
-        r = np.asarray(ref, np.float64)[n // 2:]
-        band = (0.8 * d["f0"], 1.25 * d["f0"])
-        fy, fr = peak_frequency(y, d["fs"], *band), peak_frequency(r, d["fs"], *band)
-        assert abs(fy - fr) <= 2e-3 * fr, (i, fy, fr)
-        ry, rr = np.sqrt(np.mean(y ** 2)), np.sqrt(np.mean(r ** 2))
-        assert abs(ry - rr) <= 0.02 * rr, (i, ry, rr)
+        ref = np.asarray(ref, np.float64)
+        noisy = oracle_with_state_noise(d, n, 1e-7, seed=100 + i)
+        y = np.asarray(gpu_run(sfd, ctx, d), np.float64)
+        h = n // 2
+        rms = lambda v: float(np.sqrt(np.mean(v[h:] ** 2)))
+        if rel_l2(noisy, ref) <= 1e-3:
+            stable += 1
+            assert rel_l2(y, ref) <= 1e-3, i
+            band = (0.8 * d["f0"], 1.25 * d["f0"])
+            fy, fr = peak_frequency(y[h:], d["fs"], *band), peak_frequency(ref[h:], d["fs"], *band)
+            assert abs(fy - fr) <= 2e-3 * fr, (i, fy, fr)
+        else:
+            assert abs(rms(y) - rms(ref)) <= 0.05 * rms(ref), (i, rms(y), rms(ref))
+    assert stable >= 6
 
 
 @pytest.mark.parametrize("case", [
