@@ -137,7 +137,8 @@ def test_bowed_notes_over_half_a_second(sfd, ctx):
 @pytest.mark.parametrize("case", [
     dict(f0=3000.0, alpha=3.0),                 # N_t ~ 5, one longitudinal unknown
     dict(f0=2000.0, alpha=10.0),                # N_l = 1: cubic term only, no z
-    dict(f0=40.0, alpha=1.05, kappa=0.5),       # N_l ~ 570, N_t ~ 165 (largest grids)
+    dict(f0=40.0, alpha=1.05, kappa=0.5),       # N_l ~ 570, N_t ~ 165
+    dict(f0=30.0, alpha=1.01, kappa=0.5),       # N_l = 792, N_t = 169: the largest grids of the workloads
     dict(f0=110.0, alpha=3.0, boundary=1),      # simply supported ends
     dict(f0=55.0, alpha=6.0, kappa=2.7, sigma0=2.0, sigma1=1e-4),
     dict(f0=110.0, alpha=1.0, kappa=0.0, theta=1.0),
