@@ -19,11 +19,15 @@
  *  - loss enters as 2 sigma0 delta_t. and 2 sigma1 delta_t. delta_xx (Eq. 4).
  *  - the transverse-to-longitudinal transfer is S = (h_t/h_l) R^T where R is
  *    the overlap-weight form of D_x- I_(l->t) with a linear interpolant.
+ *  - time-varying bow controls (Sec. 3.3.1) are piecewise linear in time;
+ *    the step n -> n+1 takes them at t = n k, and I, J sit at x_B(t).
  *
  * Parity status: pinned (modal closed forms, energy invariant, stability
- * bound, dense brute force on tiny grids, special cases) except the bowed
- * string beyond its first stick/slip switch, whose parity is unpinned beyond
- * the exact per-step power budget.
+ * bound, dense brute force on tiny grids, special cases). The bowed string
+ * is pinned at every step by its exact power budget and friction law and
+ * by the brute force over the steps that covers; a bowed note near a
+ * bifurcation that FP32-sized rounding crosses cannot be followed by an
+ * FP32 run beyond it, so there only its level is compared.
  */
 #ifndef SFD_ORACLE_H
 #define SFD_ORACLE_H
