@@ -37,6 +37,16 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(L, name), f"{name} declared in sfd.h but not exported"
 
 
+def test_binding_covers_every_declared_function():
+    """The Python binding gives every function of the header a signature
+    (argtypes stay None for a function the binding never declared)."""
+    B.build()
+    from paper_2311_18505_gb300 import sfd
+    L = sfd.lib()
+    missing = [n for n in declared_functions() if getattr(L, n).argtypes is None]
+    assert not missing, f"no binding for {missing}"
+
+
 def test_binding_loads_and_defaults():
     from paper_2311_18505_gb300 import sfd
     p = sfd.sfd_params_default()
