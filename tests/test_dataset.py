@@ -205,3 +205,34 @@ def test_writer_error_is_raised(tmp_path, monkeypatch):
 def test_unknown_output_is_rejected(tmp_path):
     with pytest.raises(ValueError):
         D.generate(str(tmp_path / "ds"), 2, D.Distribution(output="sideways"), render=fake_renderer())
+
+
+def test_cli_writes_a_dataset(tmp_path, monkeypatch, capsys):
+    """The command line (python -m paper_2311_18505_gb300.dataset) with a
+    stand-in for the GPU renderer: the flags reach the distribution, every
+    item is written once, and bowed items get envelopes when asked."""
+    class Fake:
+        def __init__(self, device):
+            self.render = fake_renderer()
+
+        def __call__(self, dicts):
+            return self.render(dicts)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(D, "GpuRenderer", Fake)
+    for var in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(var, raising=False)
+    out = str(tmp_path / "cli")
+    D.main(["--out", out, "--count", "5", "--seconds", "0.001", "--shard-size", "2", "--kinds", "bow",
+            "--p-bow-envelope", "1", "--no-modulation"])
+    assert json.loads(capsys.readouterr().out.strip().splitlines()[-1]) == {"out": out, "items": 5}
+    audio, index, status = D.load(out)
+    assert list(index) == list(range(5)) and audio.shape == (5, 48) and not status.any()
+    meta = [json.loads(l) for l in open(os.path.join(out, "metadata.jsonl"))]
+    assert all(m["params"]["excitation"]["kind"] == "bow" and "envelope" in m["params"]["excitation"]
+               for m in meta)
+    assert all(m["params"]["modulation"]["kind"] == "none" for m in meta)
+    info = json.load(open(os.path.join(out, "dataset.json")))
+    assert info["distribution"]["p_bow_envelope"] == 1.0 and info["shards"] == 3
