@@ -666,8 +666,9 @@ sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::
   // class launched first holds the SMs; launched last, the slowest strings
   // would start only when a lighter class drains and finish last (measured
   // on the 4096-string batch: 5.3 s per step heaviest first against 6.7 s
-  // lightest first; ordering by each class's longest job, whose length
-  // varies with the note's duration, gave 6.2 s).
+  // lightest first; ordering by the host's cost estimate of each class's
+  // longest job put the three 7-row strings behind the 3-row class, which
+  // alone has more CTAs than the GPU holds, and gave 6.2 s).
   for (int k = 0; k < kClasses; ++k) P.order[k] = kClasses - 1 - k;
   // warps per CTA: ceil(jobs / SMs), 1..4.  Warps of one CTA sit on
   // different SM sub-partitions, so pairing jobs in a CTA keeps each string
