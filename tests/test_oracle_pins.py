@@ -156,12 +156,12 @@ def test_modulated_modal_recursion(mod):
 
 @pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 150.0, "depth": 300.0, "phase": 0.4},
                                  {"kind": "gliss", "depth": 1.0, "duration": 0.00625}])
-@pytest.mark.parametrize("alpha,exi", [(3.0, 0), (6.0, 1)])
+@pytest.mark.parametrize("alpha,exi", [(3.0, 0), (6.0, 1), (2.0, 2)])
 def test_modulated_brute_force(mod, alpha, exi):
-    """Nonlinear strings with a fast vibrato or glissando on tiny grids: the
-    dense matrix form (Eqs. 7-9) with every gamma^2 term taken at the step's
-    gamma^n (transverse and longitudinal wave terms, phi') equals the oracle
-    to 1e-11 over 300 steps."""
+    """Nonlinear strings (plucked, struck, bowed) with a fast vibrato or
+    glissando on tiny grids: the dense matrix form (Eqs. 7-9) with every
+    gamma^2 term taken at the step's gamma^n (transverse and longitudinal
+    wave terms, phi') equals the oracle to 1e-11 over 300 steps."""
     d = W.make(f0=2500.0, alpha=alpha, kappa=1.0, excitation=EXCS[exi], modulation=mod)
     n_t, n_l = oracle.grid(d)
     assert n_t <= 16
