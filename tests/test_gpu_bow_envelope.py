@@ -60,6 +60,14 @@ def test_envelope_matches_oracle(sfd, ctx, f0, alpha):
     assert rel_l2(run(sfd, ctx, dict(d, excitation=BOW)), ref) > 0.1
 
 
+@pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 6.0, "depth": 40.0, "phase": 0.3},
+                                 {"kind": "gliss", "depth": 0.5, "duration": 0.0125}])
+def test_envelope_with_modulation(sfd, ctx, mod):
+    """Moving bow controls on a string whose f0 moves too (per-step gamma^n)."""
+    d = W.make(alpha=2.5, f0=196.0, excitation=dict(BOW, envelope=ENV), modulation=mod, n_samples=N)
+    assert rel_l2(run(sfd, ctx, d), oracle.run(d)) <= 1e-3
+
+
 def test_partial_envelope_and_release(sfd, ctx):
     """Only the force varies (velocity and position keep their
     sfd_excite_bow values), and the release time still cuts the force."""

@@ -191,6 +191,20 @@ def test_bow_envelope_brute_force(alpha):
     assert np.max(np.abs(y_o - y_c)) > 1e-3 * np.max(np.abs(y_o))
 
 
+def test_bow_envelope_with_vibrato_brute_force():
+    """Time-varying bow controls and a fast vibrato together: the dense
+    matrix form with the step's controls and gamma^n equals the oracle to
+    1e-11 over 400 steps."""
+    ex = dict(EXCS[2], release=-1.0, envelope=BOW_ENV)
+    mod = {"kind": "vibrato", "rate": 150.0, "depth": 300.0, "phase": 0.4}
+    d = W.make(f0=2500.0, alpha=3.0, kappa=1.0, excitation=ex, modulation=mod)
+    n_t, n_l = oracle.grid(d)
+    y_o = oracle.run(d, 400)
+    g = _wave_speeds(d, 400)
+    y_b = Brute(d, n_t, n_l).run(400, gamma_fn=lambda n: g[n])
+    assert np.max(np.abs(y_o - y_b)) <= 1e-11 * np.max(np.abs(y_b))
+
+
 def test_constant_bow_envelope_is_no_envelope():
     ex = EXCS[2]
     flat = {"t": [0.0, 0.01], "vel": [ex["vel"]] * 2, "force": [ex["force"]] * 2, "pos": [ex["pos"]] * 2}
