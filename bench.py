@@ -1,24 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: output audio samples/s of batched nonlinear string synthesis.
 
-Workload (one "step"): 256 strings, 2 s at 48 kHz each (96,000 samples),
-f0 log-uniform 40-1000 Hz, kappa U[0.5,3], alpha U[1,10], sigma0 U[0.1,2],
-sigma1 U[1e-6,1e-4], excitation uniform over pluck / hammer / bow (seed 2),
-synthesized from the initial state by one launch of the persistent step
-kernel per class.  Every step starts from freshly created strings (inputs
-resident in device memory before the timed region); L2 is flushed between
-timed steps.  `--workload modulated` times the batching workload instead:
-4096 strings of uneven N, f0 log-uniform 30-2000 Hz with vibrato or
-glissando, 4 s each, warps per CTA autotuned once, each step one CUDA-graph
-replay of the prepared launch.
+Default workload (one "step"): the batching workload, the largest that runs
+on one GPU: 4096 strings of uneven N, 4 s at 48 kHz each (192,000 samples),
+f0 log-uniform 30-2000 Hz, half with vibrato (5-7 Hz, +-20 cents), half with
+glissando (+-1 octave), kappa U[0.5,3], alpha U[1,10], sigma0 U[0.1,2],
+sigma1 U[1e-6,1e-4], excitation uniform over pluck / hammer / bow (seed 3).
+Warps per CTA are autotuned once; each step replays one captured CUDA graph
+of the prepared launch (one persistent kernel per class, concurrently) on
+freshly created strings (inputs resident in device memory before the timed
+region); L2 is flushed between timed steps.  `--workload mixed` times the
+256-string batch (2 s, f0 40-1000 Hz, seed 2) with direct launches instead.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                  [--workload mixed|modulated]
+                  [--workload modulated|mixed|serving|gradient|dataset|single]
 
-Under torchrun each rank synthesizes its own 256-string batch (weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
-`--impl reference` times the FP64 CPU oracle (the only reference this
-method has) on a bounded sample of the same workload.
+Under torchrun each rank synthesizes its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  `--impl
+reference` times the FP64 CPU oracle (the only reference this method has)
+on a bounded sample of the same workload.
 """
 
 from __future__ import annotations
@@ -44,10 +44,8 @@ from paper_2311_18505_gb300 import workloads as W  # noqa: E402
 METRIC = "output audio samples/s (all strings)"
 UNIT = "samples/s"
 FS = 48000.0
-SM_COUNT_GB300 = 152
-# FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz max SM clock
+# nominal FP32 CUDA-core rate for context: SMs x 128 FP32 lanes x 2 flops (FMA) x clock
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
 
 # Algorithmic FLOPs per grid-point update (one exact step, no repeated
 # sweeps): stencil right-hand side, matrix assembly, one exact tridiagonal
@@ -88,20 +86,20 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` on the default workload from the
-    committed ncu summary, or None when the summary is missing or was taken
-    on different kernel sources."""
+def profile_figures(name: str) -> dict | None:
+    """The "key: value" figures of a committed ncu summary (profiles/<name>),
+    or None when it is missing or was taken on other kernel sources (its
+    kernel_sources_sha256 line differs from the current sources)."""
     import re
-    path = os.path.join(ROOT, "profiles", f"{kernel}_dram_mixed256x2s.md")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    txt = open(path).read()
-    mh = re.search(r"kernel_sources_sha256: ([0-9a-f]+)", txt)
-    mb = re.search(r"dram_bytes_per_launch: (\d+)", txt)
-    if not (mh and mb) or mh.group(1) != kernel_sources_hash():
+    figs = {}
+    for m in re.finditer(r"^- ([a-z0-9_]+): ([0-9a-fA-F.e+-]+)\s*$", open(path).read(), re.M):
+        figs[m.group(1)] = m.group(2)
+    if figs.get("kernel_sources_sha256") != kernel_sources_hash():
         return None
-    return int(mb.group(1))
+    return figs
 
 
 # ----------------------------------------------------------------- clocks
@@ -209,6 +207,24 @@ def cpu_oracle_rate(strings, n_samples: int, threads: int = 0):
     return len(strings) * n_samples / dt, used, dt
 
 
+def oracle_cost(d: dict, n_samples: int) -> float:
+    """Grid-point updates of one string over n_samples (the oracle's work
+    grows with the unknowns it solves for per step)."""
+    import oracle
+    nt, nl = oracle.grid(d)
+    return ((nt - 1) + (0 if d["alpha"] == 1.0 else max(nl - 1, 0))) * float(n_samples)
+
+
+def extrapolated_rate(strings, sample, n_sample: int, seconds: float) -> float:
+    """Samples/s of the whole workload at the speed the oracle showed on a
+    sample of it: the sample's grid-point updates per second, divided into
+    the workload's grid-point updates, gives the time the workload takes."""
+    upd_rate = sum(oracle_cost(d, n_sample) for d in sample) / seconds
+    total_samples = sum(d["n_samples"] for d in strings)
+    total_updates = sum(oracle_cost(d, d["n_samples"]) for d in strings)
+    return total_samples / (total_updates / upd_rate)
+
+
 WORKLOAD_NAME = ("256 strings x 2 s at 48 kHz: f0 log-U[40,1000] Hz, kappa U[0.5,3], alpha U[1,10], "
                  "sigma0 U[0.1,2], sigma1 U[1e-6,1e-4], pluck/hammer/bow uniform (seed 2)")
 WORKLOAD_MODULATED = ("4096 strings x 4 s at 48 kHz, uneven N: f0 log-U[30,2000] Hz, half vibrato (5-7 Hz, "
@@ -246,7 +262,7 @@ def run_reference(args, ws, rank):
         return 0
     strings, workload_name = make_workload(args, 0)
     sample = strings[: args.ref_strings]
-    n = args.ref_samples
+    n = args.ref_samples or (48000 if args.workload == "modulated" else 96000)
     for _ in range(args.warmup):
         cpu_oracle_rate(sample, n)
     rates, used, dts = [], 0, []
@@ -254,13 +270,17 @@ def run_reference(args, ws, rank):
         r, used, dt = cpu_oracle_rate(sample, n)
         rates.append(r)
         dts.append(dt)
-    value = len(sample) * n * len(dts) / sum(dts)
-    desc = f"first {len(sample)} strings of the workload x {n} samples each per step"
+    # the workload's samples/s at the oracle's measured speed on the sample
+    value = extrapolated_rate(strings, sample, n, sum(dts) / len(dts))
+    desc = (f"first {len(sample)} strings of the workload x their first {n} samples per step, "
+            f"extrapolated to the whole workload by grid-point updates (sum over strings of "
+            f"(N_t - 1 + N_l - 1) x samples)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name, "reference": "FP64 CPU oracle (OpenMP)"},
+        "data": "synthetic", "config": {"workload": workload_name, "reference": "FP64 CPU oracle (OpenMP)",
+                                        "sample_rate_measured": len(sample) * n * len(dts) / sum(dts)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -278,6 +298,14 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # roofline denominators, measured on this device (clocks sampled meanwhile)
+    pclk = ClockSampler(local)
+    pclk.start()
+    peak_runs = [sfd.sfd_measure_peaks(local) for _ in range(3)]
+    time.sleep(0.45)
+    pclk_stats = pclk.stop()
+    peaks = {k: max(r[k] for r in peak_runs) for k in peak_runs[0]}
     stream = torch.cuda.Stream(dev)            # the context's stream (also the capture stream)
     torch.cuda.set_stream(stream)
     ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 4 << 30)
@@ -377,6 +405,21 @@ def run_ours(args, ws, rank, local):
     for hb, g in batches:
         del g
         free_batch(hb)
+    direct_ms = None
+    if graphed:
+        # after the timed region: one direct launch of the same prepared
+        # batch with per-class kernel events (on each class's own stream),
+        # which a graph replay does not record
+        hb = make_batch()
+        if wpc:
+            sfd.sfd_batch_set_warps_per_cta(hb[1], wpc)
+        sfd.sfd_ctx_set_timing(ctx, True)
+        flush.zero_()
+        sfd.sfd_batch_synthesize(hb[1], ns, out, offs)
+        direct_ms, _ = sfd.sfd_ctx_kernel_times(ctx)
+        sfd.sfd_ctx_set_timing(ctx, False)
+        torch.cuda.synchronize(dev)
+        free_batch(hb)
     t_total = max_over_ranks(ws, sum(times_ms) / 1e3)
     split = getattr(args, "partition", "none") == "lpt"
     value = (args.batch_samples if split else ws * total) * args.steps / t_total
@@ -415,33 +458,58 @@ def run_ours(args, ws, rank, local):
 
     if rank != 0:
         return 0
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    # dominant kernel: the class kernel with the largest average launch time
+    peak = peaks["fp32_tflops"]
+    nominal = sm_count * FP32_LANES_PER_SM * 2 * (clk["sm_max_mhz"] if clk else 2070.0) * 1e6 / 1e12
+    class_names = ["synth_kernel_reg1", "synth_kernel_reg3", "synth_kernel_reg5", "synth_kernel_reg7",
+                   "synth_kernel_reg9", "synth_kernel_smem"]
+    per_class = {}
+    src_ms = class_ms if sum(class_ms) > 0 else (direct_ms or [0.0] * len(class_names))
+    div = args.steps if sum(class_ms) > 0 else 1
+    for k in range(len(class_names)):
+        idx = {i for i, c in enumerate(classes) if c == k}
+        if not idx or src_ms[k] <= 0:
+            continue
+        f = algorithmic_flops(strings, grids, idx)
+        per_class[class_names[k]] = {"ms": src_ms[k] / div, "strings": len(idx),
+                                     "tflops": f / (src_ms[k] / div / 1e3) / 1e12}
     if sum(class_ms) > 0:
+        # dominant kernel: the class kernel with the largest average launch time
         dom = max(range(len(class_ms)), key=lambda k: class_ms[k])
         dom_ms = class_ms[dom] / args.steps
         dom_idx = {i for i, c in enumerate(classes) if c == dom}
-    else:   # graph replays: the concurrent class kernels timed together
-        dom = 0
+        kernel = class_names[dom]
+    else:
+        # graph replays: the class kernels run concurrently in one replay,
+        # timed together by the events around it on the capture stream
         dom_ms = sum(times_ms) / len(times_ms)
         dom_idx = set(range(len(strings)))
+        kernel = "synth_kernel_* (all classes, concurrent in one graph replay)"
     achieved = algorithmic_flops(strings, grids, dom_idx) / (dom_ms / 1e3) / 1e12
-    class_names = ["synth_kernel_reg1", "synth_kernel_reg3", "synth_kernel_reg5", "synth_kernel_reg7",
-                   "synth_kernel_reg9", "synth_kernel_smem"]
-    default_workload = args.workload == "mixed" and len(strings) == 256 and ws == 1 and \
-        strings[0]["n_samples"] == 96000
+    # DRAM traffic and ncu pipe / shared-memory fractions from the committed
+    # summaries of this workload's kernels (None if taken on other sources)
+    tr = profile_figures(f"synth_kernel_dram_{args.workload}.md") if ws == 1 else None
+    traffic = None
+    if tr and "dram_bytes_per_sample" in tr:
+        traffic = float(tr["dram_bytes_per_sample"]) * sum(
+            strings[i]["n_samples"] for i in dom_idx)
+    dom_class = max(per_class, key=lambda k: per_class[k]["ms"]) if per_class else None
+    sm_prof = profile_figures(f"{dom_class}_full_small.md") if dom_class else None
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        sample = strings[: args.cpu_strings]
-        rate, used, dt = cpu_oracle_rate(sample, args.cpu_samples)
-        cpu = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": f"first {len(sample)} strings of the workload x {args.cpu_samples} samples "
-                         f"({dt:.1f} s wall)"}
+        sample = strings[: args.cpu_strings or (128 if args.workload == "modulated" else 256)]
+        n_cpu = args.cpu_samples or sample[0]["n_samples"]
+        rate, used, dt = cpu_oracle_rate(sample, n_cpu)
+        extrap = extrapolated_rate(strings, sample, n_cpu, dt)
+        cpu = {"value": extrap, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"first {len(sample)} strings of the workload x {n_cpu} samples ({dt:.1f} s wall, "
+                         f"{rate:.4g} samples/s on them), extrapolated to the whole workload by grid-point "
+                         f"updates (sum over strings of (N_t - 1 + N_l - 1) x samples)"}
         # one thread, for comparison with a single-core figure (a bounded sample)
         one = strings[:16]
         r1, _, dt1 = cpu_oracle_rate(one, 24000, threads=1)
-        cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1,
-                                "sample": f"first {len(one)} strings x 24000 samples ({dt1:.1f} s wall)"}
+        cpu["single_thread"] = {"value": extrapolated_rate(strings, one, 24000, dt1), "unit": UNIT, "cores": 1,
+                                "sample": f"first {len(one)} strings x 24000 samples ({dt1:.1f} s wall), "
+                                          f"extrapolated likewise"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -454,15 +522,25 @@ def run_ours(args, ws, rank, local):
                               f"autotuned to {wpc}") if graphed else
                              "one persistent kernel per class per step, one warp per string"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": measured_traffic(class_names[dom]) if default_workload else None,
-                     "kernel": class_names[dom] if sum(class_ms) > 0 else
-                               "synth_kernel_* (all classes, concurrent in one graph replay)",
-                     "kernel_ms": dom_ms, "kernel_strings": len(dom_idx),
-                     "class_ms": {class_names[k]: class_ms[k] / args.steps for k in range(len(class_ms))
-                                  if class_ms[k] > 0},
+                     "frac": achieved / peak, "fp32_frac": achieved / peak,
+                     "smem_frac": (float(sm_prof["smem_pct_of_peak"]) / 100.0
+                                   if sm_prof and "smem_pct_of_peak" in sm_prof else None),
+                     "fma_pipe_frac": (float(sm_prof["fma_pipe_pct_of_peak"]) / 100.0
+                                       if sm_prof and "fma_pipe_pct_of_peak" in sm_prof else None),
+                     "pipe_source": (f"ncu, profiles/{dom_class}_full_small.md (kernel {dom_class}, small case)"
+                                     if sm_prof else None),
+                     "traffic": traffic,
+                     "kernel": kernel, "kernel_ms": dom_ms, "kernel_strings": len(dom_idx),
+                     "per_class": per_class,
+                     "per_class_source": ("events around each class kernel in the timed steps" if sum(class_ms) > 0
+                                          else "one direct launch of the same batch after the timed region, "
+                                               "events around each class kernel on its own stream"),
                      "step_flops_total": flops,
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived, not measured)"},
+                     "peak_note": ("of measured: FP32 FMA microbenchmark (sfd_measure_peaks, best of 3 x 5 "
+                                   "launches) on this device; nominal SMs x 128 lanes x 2 x max clock = "
+                                   f"{nominal:.1f} TFLOP/s"),
+                     "measured_peaks": dict(peaks, sm_count=sm_count,
+                                            sm_mhz_during=(pclk_stats or {}).get("sm_mhz"))},
         "grid_point_updates_per_s": ws * updates * args.steps / t_total,
         "realtime_factor": ws * total / FS * args.steps / t_total,
         "cpu_baseline": cpu,
@@ -801,8 +879,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "modulated", "serving", "gradient",
-                                                             "dataset", "single"])
+    ap.add_argument("--workload", default="modulated", choices=["modulated", "mixed", "serving", "gradient",
+                                                                 "dataset", "single"])
     ap.add_argument("--alpha", type=float, default=1.0, help="single: stiffness-to-tension ratio (1 or 3)")
     ap.add_argument("--partition", default="none", choices=["none", "lpt"],
                     help="N > 1, mixed/modulated: split one batch across the ranks by cost (strong scaling) "
@@ -817,12 +895,14 @@ def parse_args(argv=None):
                     help="1: large-grid strings may take 2 or 4 warps (sfd_ctx_set_warp_pairs)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    # oracle samples: the whole 256 x 2 s batch for the baseline (~17 s on 16
-    # cores), half of it per step for the reference arm
-    ap.add_argument("--cpu-strings", type=int, default=256)
-    ap.add_argument("--cpu-samples", type=int, default=96000)
+    # oracle samples (0: per workload).  Baseline: the first 128 strings of
+    # the 4096-string batch over their whole 4 s (~10 s on 16 cores), or the
+    # whole 256-string mixed batch; reference arm: the first 128 strings
+    # over their first second (modulated) or 2 s (mixed) per step
+    ap.add_argument("--cpu-strings", type=int, default=0)
+    ap.add_argument("--cpu-samples", type=int, default=0)
     ap.add_argument("--ref-strings", type=int, default=128)
-    ap.add_argument("--ref-samples", type=int, default=96000)
+    ap.add_argument("--ref-samples", type=int, default=0)
     return ap.parse_args(argv)
 
 

@@ -124,6 +124,13 @@ sfd_status sfd_string_info(const sfd_string* s, int32_t* n_t, int32_t* n_l, doub
  * Errors as sfd_string_create's parameter checks. */
 sfd_status sfd_grid(const sfd_string_params* p, int32_t* n_t, int32_t* n_l);
 
+/* Grid-sizing ratio of an f0 modulation: the largest gamma^n / gamma it
+ * reaches (vibrato 2^{|c| / 1200}, glissando 2^{max(D, 0)}, none 1), the
+ * f0_max_ratio at which a grid holds the whole note (Sec. 1's varying f0
+ * on the fixed grid of Sec. 3.2).  SFD_EINVAL for an unknown kind or a
+ * non-finite depth. */
+sfd_status sfd_modulation_peak(int32_t kind, double depth, double* ratio);
+
 /* Pluck (Sec. 3.3): initial condition u^0 = u^1 = triangle of peak amp/L at
  * pos (fraction of L), zero initial velocity.  Valid only before the first
  * synthesize call (else SFD_ESTATE). */
@@ -158,8 +165,13 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
 
 /* f0 modulation (Sec. 1): kind SFD_MOD_VIBRATO, gamma^n = gamma 2^{(c/1200)
  * sin(2 pi rate t + phase)} with depth c in cents; SFD_MOD_GLISS, gamma^n =
- * gamma 2^{D t / duration} with depth D in octaves.  The grid must have been
- * sized for the peak (f0_max_ratio), else SFD_EINVAL. */
+ * gamma 2^{D t / duration} with depth D in octaves.  The grid must hold the
+ * modulation's peak wave speed (sfd_modulation_peak): when the string was
+ * created with a smaller f0_max_ratio, its grid is derived again for the
+ * peak (N_t and N_l may grow; the excitation keeps its parameters and
+ * position; a new pool block holds the larger state), SFD_ENOMEM if the
+ * pool has no room, SFD_EBUSY for a string already in a batch.  Before the
+ * first synthesize call only (else SFD_ESTATE). */
 sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth,
                               double phase_rad, double duration_s);
 
@@ -282,19 +294,24 @@ typedef struct {
  * `params` and `exc` exactly as sfd_string_create + sfd_excite_* would, into
  * out_device (device memory on `device`), without allocating any device
  * memory.  For callers that cannot call cudaMalloc: real-time audio threads
- * (it can synchronise the device and block for an unbounded time), code
- * running while a stream is captured, hosts that fix a library's device
- * footprint in advance.  There is no counterpart in the paper.
+ * (cudaMalloc can synchronise the device and block for an unbounded time)
+ * and hosts that fix a library's device footprint in advance.  There is no
+ * counterpart in the paper.
  *
  * The string's descriptor, state, job entry and work-queue counter live in
  * one static device array of SFD_NOALLOC_SCRATCH_BYTES that every GPU
  * loading this library keeps until the process exits; strings that need
- * more get SFD_EINVAL.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current: make it
- * before any stream capture.  Every call shares the array and overwrites it,
- * so calls that overlap on the GPU (from several threads or streams) race:
- * serialise them.  The call waits for its stream before returning (it reads
- * the string's status).  f0 modulation is not available here. */
+ * more, or more shared memory than one warp may have, get SFD_EINVAL.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current.  Every call shares the
+ * array and overwrites it, so calls that overlap on the GPU (from several
+ * threads or streams) race: serialise them.  The call copies from host
+ * memory and waits for its stream before returning (it reads the string's
+ * status), so it cannot be captured into a CUDA graph: on a capturing
+ * stream it returns SFD_EINVAL and enqueues nothing.  Parameters are
+ * validated whatever n_samples is; n_samples = 0 then returns SFD_OK and
+ * writes nothing.  The caller's current device is the same on return.
+ * f0 modulation is not available here. */
 sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, const sfd_string_params* params,
                                   const sfd_excitation* exc, int64_t n_samples, float* out_device);
 
@@ -415,6 +432,18 @@ sfd_status sfd_tape_forward(sfd_tape* t, float* y_device);
 /* SFD_ESTATE before a forward. */
 sfd_status sfd_tape_backward(sfd_tape* t, const float* dy_device, double* grad);
 sfd_status sfd_tape_destroy(sfd_tape* t);
+
+/* Throughput peaks of device `device`, measured by three short
+ * microbenchmarks timed with CUDA events (best of five launches after a
+ * warm-up; no counterpart in the paper): FP32 and FP64 fused multiply-add
+ * throughput [TFLOP/s, 2 flops per FMA] and conflict-free 16-byte
+ * shared-memory load bandwidth [TB/s] over all SMs.  These are the
+ * denominators of the step kernels' roofline: they are bound by FP32
+ * arithmetic, shared-memory traffic and per-step latency, not by HBM.
+ * Allocates and frees a small device buffer; the caller's current device
+ * is the same on return.  SFD_EINVAL for NULL outputs, SFD_ECUDA on a CUDA
+ * error. */
+sfd_status sfd_measure_peaks(int device, double* fp32_tflops, double* fp64_tflops, double* smem_tbs);
 
 /* Thread-local message describing the last error. */
 const char* sfd_last_error(void);

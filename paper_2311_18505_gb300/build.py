@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 # (source, object, extra flags): the step kernel is compiled once per
 # transverse rows-per-lane class so each kernel gets its own register budget
-UNITS = [("sfd_api.cu", "sfd_api.o", []), ("sfd_adjoint.cu", "sfd_adjoint.o", [])] + \
+UNITS = [("sfd_api.cu", "sfd_api.o", []), ("sfd_adjoint.cu", "sfd_adjoint.o", []),
+         ("sfd_peaks.cu", "sfd_peaks.o", [])] + \
         [("sfd_kernel.cu", f"sfd_kernel_r{mu}.o", [f"-DSFD_MU={mu}"]) for mu in (1, 3, 5, 7, 9)] + \
         [("sfd_kernel.cu", "sfd_kernel_smem.o", [])]
 SOURCES = sorted({u[0] for u in UNITS})

@@ -38,6 +38,8 @@
 // errors against the FP64 oracle's gradient in FP32, none in FP64).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "sfd_device.cuh"
 
 namespace sfd {
@@ -575,9 +577,37 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   }
 }
 
+namespace {
+// The dynamic shared-memory limit is a process-wide attribute of the
+// kernel: raised once per device to the opt-in maximum and never lowered,
+// so concurrent launches from other threads cannot shrink it under a launch.
+constexpr int kMaxAdjDevices = 64;
+std::mutex g_adj_attr_mu;
+bool g_adj_attr_done[kMaxAdjDevices] = {};
+
+cudaError_t raise_adjoint_smem_limit() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxAdjDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_adj_attr_mu);
+  if (g_adj_attr_done[dev]) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, adjoint_kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - static_cast<int>(fa.sharedSizeBytes));
+  if (e == cudaSuccess) g_adj_attr_done[dev] = true;
+  return e;
+}
+}  // namespace
+
 // Host-side launcher (called by sfd_api.cu): one warp per job.
 cudaError_t launch_adjoint(const AdjJob* d_jobs, int n_jobs, int smem_bytes, cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  cudaError_t e = raise_adjoint_smem_limit();
   if (e != cudaSuccess) return e;
   adjoint_kernel<<<n_jobs, kWarp, static_cast<size_t>(smem_bytes), stream>>>(d_jobs, n_jobs);
   return cudaGetLastError();

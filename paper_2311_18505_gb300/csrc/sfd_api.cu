@@ -168,6 +168,7 @@ struct sfd_string {
   double pluck_amp = 0, pluck_pos = 0.5;
   double hammer_uh1 = 0;    // u_H^1 = v_H k (normalised), u_H^0 = 0
   double bow_pos = 0.5;     // x_B of sfd_excite_bow (constant position of an envelope)
+  double exc_pos = 0.5;     // hammer or bow position (excitation node after a regrid)
 };
 
 struct sfd_batch {
@@ -534,6 +535,7 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
     s->pluck_amp = 0;
     fill_desc(s);
     point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+    s->exc_pos = pos;
     s->h.ham_M = static_cast<float>(ex.mass_kg / (q.linear_density * q.length_m));
     s->h.ham_k2w = static_cast<float>(s->k * s->k * std::pow(ex.omega_h, 1.0 + ex.alpha_h));
     s->h.ham_expo = static_cast<float>(ex.alpha_h - 1.0);
@@ -545,6 +547,7 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
     s->pluck_amp = 0;
     fill_desc(s);
     point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+    s->exc_pos = pos;
     s->h.bow_F = static_cast<float>(ex.force_n / (q.linear_density * q.length_m * q.length_m));
     s->h.bow_v = static_cast<float>(ex.vel_mps / q.length_m);
     s->h.bow_a = static_cast<float>(ex.a_s_per_m * q.length_m);
@@ -562,6 +565,33 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
   } else {
     return fail(SFD_EINVAL, "bad excitation kind %d", ex.kind);
   }
+  return SFD_OK;
+}
+
+// Largest wave-speed ratio gamma^n / gamma a modulation reaches (reading
+// A14): vibrato 2^{|c| / 1200}, glissando 2^{max(D, 0)}; 1 without one.
+double modulation_peak(int32_t kind, double depth) {
+  if (kind == SFD_MOD_VIBRATO) return std::pow(2.0, std::fabs(depth) / 1200.0);
+  if (kind == SFD_MOD_GLISS) return std::pow(2.0, std::max(0.0, depth));
+  return 1.0;
+}
+
+// Re-derive the grid of a string (host copy) for the peak wave speed
+// gamma * ratio (reading A14: the grid of a modulated note is the one of its
+// largest gamma): N_t, N_l, the descriptor and the excitation point.  The
+// excitation's other fields, a bow envelope and the pluck (sampled on the
+// grid when the block is written) carry over.
+sfd_status regrid_host(sfd_string* s, double ratio) {
+  sfd_string_params q = s->p;
+  q.f0_max_ratio = ratio;
+  int n_t = 0, n_l = 0;
+  sfd_status rc = derive_grid(q, s->gamma * ratio, &n_t, &n_l);
+  if (rc) return rc;
+  s->p = q;
+  s->n_t = n_t;
+  s->n_l = n_l;
+  fill_desc(s);
+  if (s->exc != kPluck) point_weights(s->n_t, s->exc_pos, &s->h.e_node, &s->h.e_w);
   return SFD_OK;
 }
 
@@ -894,6 +924,15 @@ sfd_status sfd_grid(const sfd_string_params* p, int32_t* n_t, int32_t* n_l) {
   return SFD_OK;
 }
 
+sfd_status sfd_modulation_peak(int32_t kind, double depth, double* ratio) {
+  if (!ratio) return fail(SFD_EINVAL, "ratio is NULL");
+  if (kind != SFD_MOD_NONE && kind != SFD_MOD_VIBRATO && kind != SFD_MOD_GLISS)
+    return fail(SFD_EINVAL, "bad modulation kind");
+  if (!std::isfinite(depth)) return fail(SFD_EINVAL, "bad modulation depth");
+  *ratio = modulation_peak(kind, depth);
+  return SFD_OK;
+}
+
 sfd_status sfd_ctx_set_warp_pairs(sfd_ctx* c, int32_t enable) {
   if (!c) return fail(SFD_EINVAL, "ctx is NULL");
   c->warp_pairs = enable != 0;
@@ -986,6 +1025,7 @@ sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, doub
   s->exc = kHammer;
   fill_desc(s);
   point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+  s->exc_pos = pos;
   s->h.ham_M = static_cast<float>(mass_kg / (p.linear_density * p.length_m));
   s->h.ham_k2w = static_cast<float>(s->k * s->k * std::pow(omega_h, 1.0 + alpha_h));
   s->h.ham_expo = static_cast<float>(alpha_h - 1.0);
@@ -1009,6 +1049,7 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   s->pluck_amp = 0;
   fill_desc(s);
   point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
+  s->exc_pos = pos;
   s->h.bow_F = static_cast<float>(force_n / (p.linear_density * p.length_m * p.length_m));
   s->h.bow_v = static_cast<float>(vel_mps / p.length_m);
   s->h.bow_a = static_cast<float>(a_s_per_m * p.length_m);
@@ -1073,6 +1114,29 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
                               double duration_s) {
   if (!s) return fail(SFD_EINVAL, "string is NULL");
   if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
+  const double peak = std::isfinite(depth) ? modulation_peak(kind, depth) : 1.0;
+  if (peak > s->p.f0_max_ratio * (1.0 + 1e-12)) {
+    // the grid grows to the modulation's peak: a new pool block for the
+    // larger state (nothing has run on the old one)
+    if (s->batch_refs > 0)
+      return fail(SFD_EBUSY, "the grid must grow to this modulation's peak: set it before adding the string to a batch");
+    sfd_ctx* c = s->ctx;
+    const sfd_string saved = *s;
+    sfd_status rg = regrid_host(s, peak);
+    if (rg == SFD_OK &&
+        static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z, s->h.z_jacobi)) * sizeof(float) > c->smem_optin)
+      rg = fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", s->n_t, s->n_l);
+    char* nb = nullptr;
+    if (rg == SFD_OK && !(nb = c->pool.alloc(block_bytes(s->h))))
+      rg = fail(SFD_ENOMEM, "device pool exhausted (%zu of %zu bytes used)", c->pool.used(), c->pool.size());
+    if (rg) {
+      *s = saved;
+      return rg;
+    }
+    c->pool.dealloc(saved.block);
+    s->block = nb;
+    carve(s);
+  }
   sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
   if (rc) return rc;
   stage_initial(s);
@@ -1428,23 +1492,34 @@ sfd_status sfd_batch_destroy(sfd_batch* b) {
 // Synthesis without device allocation.
 //
 // Callers that must not allocate device memory -- a real-time audio callback
-// (cudaMalloc can synchronise the device and block for an unbounded time),
-// code running while a stream is being captured into a CUDA graph, or a host
-// that fixes a library's device footprint up front -- use this one entry
-// point instead of a context.  Everything the step kernel needs beyond the
-// caller's output buffer (the string's descriptor and state, the job entry
-// and the work-queue counter) lives in one file-scope device array of
-// kNoAllocBytes, which every GPU that loads this library keeps until exit.
+// (cudaMalloc can synchronise the device and block for an unbounded time), or
+// a host that fixes a library's device footprint up front -- use this one
+// entry point instead of a context.  Everything the step kernel needs beyond
+// the caller's output buffer (the string's descriptor and state, the job
+// entry and the work-queue counter) lives in one file-scope device array of
+// SFD_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library keeps
+// until exit.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kNoAllocBytes = 32u * 1024u;
+constexpr size_t kNoAllocBytes = SFD_NOALLOC_SCRATCH_BYTES;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};      // device address of the array, per device
 size_t g_noalloc_smem[kMaxDevices] = {};    // opt-in shared memory per block, per device
+
+// Puts back the caller's current device on every return path.
+struct DeviceRestore {
+  int dev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  }
+  ~DeviceRestore() {
+    if (dev >= 0) cudaSetDevice(dev);
+  }
+};
 
 }  // namespace
 
@@ -1454,9 +1529,45 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
   if (n_samples < 0) return fail(SFD_EINVAL, "n_samples < 0");
   if (n_samples > 0 && !out_device) return fail(SFD_EINVAL, "out_device is NULL");
   if (device < 0 || device >= kMaxDevices) return fail(SFD_EINVAL, "device %d out of range", device);
+
+  // the string, as sfd_string_create + sfd_excite_* would set it up (host
+  // arithmetic only: invalid parameters are refused whatever n_samples is)
+  sfd_string s;
+  sfd_status rc = init_host_string(*params, &s);
+  if (rc) return rc;
+  if ((rc = apply_excitation(&s, *exc))) return rc;
+  const int n_t = s.n_t, n_l = s.n_l;
+  const Desc& D = s.h;
+  // layout inside the array: Desc | Scalars | u du z dz xz az | Job | counters
+  const size_t nz = D.n_z > 0 ? D.n_z : 1;
+  size_t off = 0;
+  auto place = [&](size_t n) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    const size_t at = off;
+    off += n;
+    return at;
+  };
+  const size_t o_desc = place(sizeof(Desc)), o_sc = place(sizeof(Scalars));
+  const size_t o_u = place(sizeof(float) * D.n_u), o_du = place(sizeof(float) * D.n_u);
+  const size_t o_z = place(sizeof(float) * nz), o_dz = place(sizeof(float) * nz);
+  const size_t o_xz = place(sizeof(float) * nz), o_az = place(sizeof(float) * nz);
+  const size_t o_job = place(sizeof(Job)), o_cnt = place(sizeof(int) * kClasses);
+  if (off > kNoAllocBytes)
+    return fail(SFD_EINVAL,
+                "string needs %zu bytes of scratch (N_t=%d, N_l=%d); the no-allocation entry point holds %zu",
+                off, n_t, n_l, kNoAllocBytes);
+
+  DeviceRestore restore;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  // The call copies from host memory it frees on return and waits for its
+  // stream, neither of which a captured graph can hold.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(SFD_EINVAL, "the stream is capturing: the no-allocation entry point cannot be captured");
   void* base = nullptr;
   size_t smem_optin = 0;
   {
@@ -1476,36 +1587,10 @@ extern "C" sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, cons
     base = g_noalloc_ptr[device];
     smem_optin = g_noalloc_smem[device];
   }
-  if (n_samples == 0) return SFD_OK;
-
-  // the string, as sfd_string_create + sfd_excite_* would set it up
-  sfd_string s;
-  sfd_status rc = init_host_string(*params, &s);
-  if (rc) return rc;
-  if ((rc = apply_excitation(&s, *exc))) return rc;
-  const int n_t = s.n_t, n_l = s.n_l;
-  const Desc& D = s.h;
   const size_t wbytes = static_cast<size_t>(warp_smem_floats(D.m_u, D.m_z, D.z_jacobi)) * sizeof(float);
   if (wbytes > smem_optin) return fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", n_t, n_l);
+  if (n_samples == 0) return SFD_OK;
 
-  // layout inside the array: Desc | Scalars | u du z dz xz az | Job | counters
-  const size_t nz = D.n_z > 0 ? D.n_z : 1;
-  size_t off = 0;
-  auto place = [&](size_t n) {
-    off = (off + kAlign - 1) / kAlign * kAlign;
-    const size_t at = off;
-    off += n;
-    return at;
-  };
-  const size_t o_desc = place(sizeof(Desc)), o_sc = place(sizeof(Scalars));
-  const size_t o_u = place(sizeof(float) * D.n_u), o_du = place(sizeof(float) * D.n_u);
-  const size_t o_z = place(sizeof(float) * nz), o_dz = place(sizeof(float) * nz);
-  const size_t o_xz = place(sizeof(float) * nz), o_az = place(sizeof(float) * nz);
-  const size_t o_job = place(sizeof(Job)), o_cnt = place(sizeof(int) * kClasses);
-  if (off > kNoAllocBytes)
-    return fail(SFD_EINVAL,
-                "string needs %zu bytes of scratch (N_t=%d, N_l=%d); the no-allocation entry point holds %zu",
-                off, n_t, n_l, kNoAllocBytes);
   char* b = static_cast<char*>(base);
   s.h.u = reinterpret_cast<float*>(b + o_u);
   s.h.du = reinterpret_cast<float*>(b + o_du);

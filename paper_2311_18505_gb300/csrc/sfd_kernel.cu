@@ -26,6 +26,8 @@
 // through the unit-force response A^{-1} J solved alongside.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "sfd_step_smem.cuh"
 #include "sfd_step_reg.cuh"
 
@@ -96,6 +98,37 @@ __global__ void __launch_bounds__(128, 1) SFD_KERNEL(const Job* __restrict__ job
   }
 }
 
+// The kernel's dynamic shared-memory limit is a process-wide attribute of
+// the function on each device.  It is raised once per device to everything
+// a block may opt into (minus the kernel's static shared memory) and never
+// lowered, so launches from several threads or contexts cannot undo one
+// another's setting between setting and launching; each launch still asks
+// for only the bytes its strings need.
+namespace {
+constexpr int kMaxAttrDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_done[kMaxAttrDevices] = {};
+
+cudaError_t raise_smem_limit() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxAttrDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_attr_done[dev]) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, SFD_KERNEL);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(SFD_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - static_cast<int>(fa.sharedSizeBytes));
+  if (e == cudaSuccess) g_attr_done[dev] = true;
+  return e;
+}
+}  // namespace
+
 // Host-side launcher of this class (C++ linkage, called by sfd_api.cu).  The
 // job counter is cleared on the same stream before the kernel starts.  With
 // group = 2 or 4 (register classes; warps_per_cta a multiple of it, 4 for
@@ -110,8 +143,7 @@ cudaError_t SFD_LAUNCHER(const Job* d_jobs, int n_jobs, int* d_counter, int warp
   if (warps_per_cta % group != 0 || (group == 4 && warps_per_cta != 4)) return cudaErrorInvalidValue;
   const int regions = warps_per_cta / group;
   const size_t smem = static_cast<size_t>(warp_floats) * regions * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(SFD_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = raise_smem_limit();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d_counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;

@@ -161,7 +161,10 @@ static sfd_status submit_note(sfd_server* sv, const sfd_request* r, int32_t env_
   if (r->n_samples <= 0) return fail(SFD_EINVAL, "n_samples must be > 0");
   sfd_string* s = new (std::nothrow) sfd_string();
   if (!s) return fail(SFD_ENOMEM, "host allocation failed");
-  sfd_status rc = init_host_string(r->params, s);
+  // the grid is sized for the modulation's peak wave speed (reading A14)
+  sfd_string_params q = r->params;
+  if (std::isfinite(r->mod_depth)) q.f0_max_ratio = std::max(q.f0_max_ratio, modulation_peak(r->mod_kind, r->mod_depth));
+  sfd_status rc = init_host_string(q, s);
   if (rc == SFD_OK) rc = apply_excitation(s, r->exc);
   if (rc == SFD_OK && env_n > 0) rc = apply_bow_envelope(s, env_n, env_t, env_v, env_f, env_x);
   if (rc == SFD_OK) rc = apply_modulation(s, r->mod_kind, r->mod_rate_hz, r->mod_depth, r->mod_phase_rad,

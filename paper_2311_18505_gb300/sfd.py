@@ -24,6 +24,7 @@ SFD_ECUDA, SFD_ETIMEOUT, SFD_EBUSY, SFD_ESTATE = -5, -6, -7, -8
 STATUS_NAMES = {0: "SFD_OK", -1: "SFD_EINVAL", -2: "SFD_ENOMEM", -3: "SFD_EUNSTABLE", -4: "SFD_ENOCONV",
                 -5: "SFD_ECUDA", -6: "SFD_ETIMEOUT", -7: "SFD_EBUSY", -8: "SFD_ESTATE"}
 SFD_MOD_NONE, SFD_MOD_VIBRATO, SFD_MOD_GLISS = 0, 1, 2
+MOD_KINDS = {"none": SFD_MOD_NONE, "vibrato": SFD_MOD_VIBRATO, "gliss": SFD_MOD_GLISS}
 SFD_OUTPUT_TRANSVERSE, SFD_OUTPUT_LONGITUDINAL = 0, 1
 OUTPUTS = {"transverse": SFD_OUTPUT_TRANSVERSE, "longitudinal": SFD_OUTPUT_LONGITUDINAL}
 
@@ -115,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "sfd_excite_bow": (i32, [vp, dbl, dbl, dbl, dbl, dbl, dbl]),
         "sfd_bow_envelope": (i32, [vp, i32, P(dbl), P(dbl), P(dbl), P(dbl)]),
         "sfd_set_modulation": (i32, [vp, i32, dbl, dbl, dbl, dbl]),
+        "sfd_modulation_peak": (i32, [i32, dbl, P(dbl)]),
         "sfd_synthesize": (i32, [vp, i64, vp, i32]),
         "sfd_string_position": (i32, [vp, P(i64), P(i64)]),
         "sfd_string_state": (i32, [vp, vp, vp, vp, vp]),
@@ -147,6 +149,7 @@ def lib() -> ctypes.CDLL:
         "sfd_tape_forward": (i32, [vp, vp]),
         "sfd_tape_backward": (i32, [vp, vp, P(dbl)]),
         "sfd_tape_destroy": (i32, [vp]),
+        "sfd_measure_peaks": (i32, [ctypes.c_int, P(dbl), P(dbl), P(dbl)]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -233,6 +236,13 @@ def sfd_bow_envelope(s: int, t_s, vel_mps=None, force_n=None, pos=None) -> None:
 def sfd_set_modulation(s: int, kind: int, rate_hz: float = 0.0, depth: float = 0.0, phase_rad: float = 0.0,
                        duration_s: float = 0.0) -> None:
     _check(lib().sfd_set_modulation(s, kind, rate_hz, depth, phase_rad, duration_s))
+
+
+def sfd_modulation_peak(kind: int, depth: float) -> float:
+    """Grid-sizing ratio (largest gamma^n / gamma) of an f0 modulation."""
+    r = ctypes.c_double()
+    _check(lib().sfd_modulation_peak(kind, depth, ctypes.byref(r)))
+    return r.value
 
 
 def sfd_synthesize(s: int, n_samples: int, out=None, allow_noconv: bool = False):
@@ -378,6 +388,14 @@ def sfd_string_kernel_class(s: int) -> int:
     c = ctypes.c_int32()
     _check(lib().sfd_string_kernel_class(s, ctypes.byref(c)))
     return c.value
+
+
+def sfd_measure_peaks(device: int = 0) -> dict:
+    """Measured FP32 / FP64 FMA throughput [TFLOP/s] and shared-memory load
+    bandwidth [TB/s] of the device (the roofline denominators)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sfd_measure_peaks(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value, "smem_tbs": c.value}
 
 
 def sfd_last_error() -> str:
@@ -557,12 +575,8 @@ def params_from_dict(d: dict) -> sfd_string_params:
     p.pickup_pos = d.get("pickup", 0.7)
     p.output = OUTPUTS[d.get("output", "transverse")]
     mod = d.get("modulation", {"kind": "none"})
-    ratio = 1.0
-    if mod.get("kind") == "vibrato":
-        ratio = 2.0 ** (abs(mod["depth"]) / 1200.0)
-    elif mod.get("kind") == "gliss":
-        ratio = 2.0 ** max(0.0, mod["depth"])
-    p.f0_max_ratio = d.get("gamma_max_ratio", ratio)
+    kind = MOD_KINDS[mod.get("kind", "none")]
+    p.f0_max_ratio = d.get("gamma_max_ratio", sfd_modulation_peak(kind, mod.get("depth", 0.0)))
     return p
 
 

@@ -248,3 +248,35 @@ def test_warp_pairs_change_nothing(sfd):
                 assert np.array_equal(x, y)
     finally:
         sfd.sfd_ctx_destroy(ctx)
+
+
+def test_modulation_grows_the_grid_before_the_first_synthesis(sfd):
+    """A string created without room for its modulation's peak (f0_max_ratio
+    1) gets the grid of that peak from sfd_set_modulation (reading A14), with
+    its hammer at the same position: grid and samples equal a string sized
+    for the peak at creation, bit for bit.  In a batch the grid can no
+    longer change (SFD_EBUSY)."""
+    ctx = sfd.sfd_ctx_create(0, None, 64 << 20)
+    try:
+        d = W.make(f0=150.0, kappa=1.2, alpha=3.0, n_samples=3000,
+                   excitation={"kind": "hammer", "mass": 5e-3, "vel": 2.0, "pos": 0.27, "omega": 3000.0,
+                               "alpha": 2.5},
+                   modulation={"kind": "gliss", "depth": 1.0, "duration": 0.0625})
+        sized = sfd.string_from_dict(ctx, d)
+        late = sfd.string_from_dict(ctx, dict(d, gamma_max_ratio=1.0, modulation={"kind": "none"}))
+        small = sfd.sfd_string_info(late)[:2]
+        sfd.sfd_set_modulation(late, sfd.SFD_MOD_GLISS, 0.0, 1.0, 0.0, 0.0625)
+        assert sfd.sfd_string_info(late)[:2] == sfd.sfd_string_info(sized)[:2] == sfd.sfd_grid(sfd.params_from_dict(d))
+        assert sfd.sfd_string_info(late)[0] > small[0]
+        assert np.array_equal(sfd.sfd_synthesize(late, 3000), sfd.sfd_synthesize(sized, 3000))
+        sfd.sfd_string_destroy(late)
+        sfd.sfd_string_destroy(sized)
+        s = sfd.string_from_dict(ctx, dict(d, gamma_max_ratio=1.0, modulation={"kind": "none"}))
+        b = sfd.sfd_batch_create(ctx, [s])
+        with pytest.raises(sfd.SfdError) as ei:
+            sfd.sfd_set_modulation(s, sfd.SFD_MOD_GLISS, 0.0, 1.0, 0.0, 0.0625)
+        assert ei.value.code == sfd.SFD_EBUSY
+        sfd.sfd_batch_destroy(b)
+        sfd.sfd_string_destroy(s)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)

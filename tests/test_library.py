@@ -159,6 +159,22 @@ def test_host_grid_matches_the_oracle():
     assert ei.value.code == sfd.SFD_EINVAL
 
 
+def test_modulation_peak_matches_the_oracle():
+    """The library's grid-sizing ratio of a modulation (host arithmetic)
+    equals the oracle's own reading of it, and refuses bad input."""
+    import oracle
+    from paper_2311_18505_gb300 import sfd
+    cases = [("vibrato", 20.0), ("vibrato", -35.0), ("gliss", 1.0), ("gliss", -1.0), ("gliss", 0.37),
+             ("none", 0.0)]
+    for kind, depth in cases:
+        assert sfd.sfd_modulation_peak(sfd.MOD_KINDS[kind], depth) == \
+            oracle.gamma_max_ratio({"kind": kind, "depth": depth})
+    for kind, depth in ((7, 1.0), (1, float("nan"))):
+        with pytest.raises(sfd.SfdError) as ei:
+            sfd.sfd_modulation_peak(kind, depth)
+        assert ei.value.code == sfd.SFD_EINVAL
+
+
 def test_lpt_partition():
     """Every string on exactly one rank, the same split however often it is
     computed, and the greedy bound: no rank above the mean load plus the

@@ -42,8 +42,8 @@ def _bench_rank(rank, port, out):
         m = bench.max_over_ranks(ws, 1.5 + rank)
         args = bench.parse_args(["--gpus", str(WORLD)])
         strings, _ = bench.make_workload(args, rank)
-        split_args = bench.parse_args(["--gpus", str(WORLD), "--partition", "lpt", "--strings", "64",
-                                       "--seconds", "0.5"])
+        split_args = bench.parse_args(["--gpus", str(WORLD), "--workload", "mixed", "--partition", "lpt",
+                                       "--strings", "64", "--seconds", "0.5"])
         split, _ = bench.make_workload(split_args, rank)
         ref = bench.run_reference(bench.parse_args(["--impl", "reference"]), ws, rank) if rank else None
         with open(os.path.join(out, f"bench{rank}.json"), "w") as f:
@@ -57,8 +57,8 @@ def test_bench_rank_helpers(tmp_path):
     mp.spawn(_bench_rank, args=(free_port(), str(tmp_path)), nprocs=WORLD, join=True)
     got = [json.load(open(tmp_path / f"bench{r}.json")) for r in range(WORLD)]
     assert all(g["max"] == 1.5 + WORLD - 1 for g in got)
-    # each rank its own 256-string batch (weak scaling)
-    assert len(got[0]["f0"]) == len(got[1]["f0"]) == 256
+    # each rank its own 4096-string batch (weak scaling)
+    assert len(got[0]["f0"]) == len(got[1]["f0"]) == 4096
     assert not set(got[0]["f0"]) & set(got[1]["f0"])
     # the reference arm runs on rank 0 alone; the others return without work
     assert got[1]["ref"] == 0
