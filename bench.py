@@ -308,9 +308,13 @@ def run_ours(args, ws, rank, local):
     peaks = {k: max(r[k] for r in peak_runs) for k in peak_runs[0]}
     stream = torch.cuda.Stream(dev)            # the context's stream (also the capture stream)
     torch.cuda.set_stream(stream)
-    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, 4 << 30)
-    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
     strings, workload_name = make_workload(args, rank)
+    # the device pool holds every prepared batch's strings and, for the
+    # end-to-end leg, the whole step's output
+    out_bytes = 4 * sum(d["n_samples"] for d in strings)
+    pool = (256 << 20) + (0 if args.no_e2e else out_bytes) + (args.steps + 1) * len(strings) * (48 << 10)
+    ctx = sfd.sfd_ctx_create(local, stream.cuda_stream, pool)
+    sfd.sfd_ctx_set_warp_pairs(ctx, bool(args.warp_groups))
     graphed = args.workload == "modulated"
     ns = np.array([d["n_samples"] for d in strings], dtype=np.int64)
     offs = np.zeros(len(ns), dtype=np.int64)
@@ -340,10 +344,10 @@ def run_ours(args, ws, rank, local):
     updates = sum(((nt - 1) + (0 if d["alpha"] == 1.0 else max(nl - 1, 0))) * (d["n_samples"] - 2)
                   for d, (nt, nl) in zip(strings, grids))
 
-    wpc = 0
+    wpc = args.warps_per_cta
     if not graphed:
         sfd.sfd_ctx_set_timing(ctx, True)
-    if graphed:   # autotune warps per CTA once, on throwaway copies
+    if graphed and not wpc:   # autotune warps per CTA once, on throwaway copies
         hb = make_batch()
         wpc = sfd.sfd_batch_autotune(hb[1], 2048)
         free_batch(hb)
@@ -519,7 +523,7 @@ def run_ours(args, ws, rank, local):
                    "seconds": float(strings[0]["n_samples"] / FS), "fs": FS,
                    "samples_per_step": total, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": ("one CUDA-graph replay per step (concurrent class kernels), warps per CTA "
-                              f"autotuned to {wpc}") if graphed else
+                              f"{'set' if args.warps_per_cta else 'autotuned'} to {wpc}") if graphed else
                              "one persistent kernel per class per step, one warp per string"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "fp32_frac": achieved / peak,
@@ -894,6 +898,8 @@ def parse_args(argv=None):
     ap.add_argument("--warp-groups", type=int, default=1, choices=[0, 1],
                     help="1: large-grid strings may take 2 or 4 warps (sfd_ctx_set_warp_pairs)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--warps-per-cta", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="modulated: warps per CTA (0: autotuned once before the warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # oracle samples (0: per workload).  Baseline: the first 128 strings of
     # the 4096-string batch over their whole 4 s (~10 s on 16 cores), or the

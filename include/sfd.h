@@ -165,13 +165,13 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
 
 /* f0 modulation (Sec. 1): kind SFD_MOD_VIBRATO, gamma^n = gamma 2^{(c/1200)
  * sin(2 pi rate t + phase)} with depth c in cents; SFD_MOD_GLISS, gamma^n =
- * gamma 2^{D t / duration} with depth D in octaves.  The grid must hold the
- * modulation's peak wave speed (sfd_modulation_peak): when the string was
- * created with a smaller f0_max_ratio, its grid is derived again for the
- * peak (N_t and N_l may grow; the excitation keeps its parameters and
- * position; a new pool block holds the larger state), SFD_ENOMEM if the
- * pool has no room, SFD_EBUSY for a string already in a batch.  Before the
- * first synthesize call only (else SFD_ESTATE). */
+ * gamma 2^{D t / duration} with depth D in octaves.  The grid must be stable
+ * at the modulation's peak wave speed (sfd_modulation_peak): when the string
+ * was created with a smaller f0_max_ratio, its grid is derived again for the
+ * peak (a faster wave needs a coarser grid, so N_t and N_l shrink; the
+ * excitation keeps its parameters and position; a new pool block holds the
+ * state), SFD_ENOMEM if the pool has no room, SFD_EBUSY for a string already
+ * in a batch.  Before the first synthesize call only (else SFD_ESTATE). */
 sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth,
                               double phase_rad, double duration_s);
 
@@ -188,6 +188,17 @@ sfd_status sfd_string_position(const sfd_string* s, int64_t* time_level, int64_t
 /* Copy the state to host FP32 arrays: u^{n-1}, u^n (N_t - 1 each),
  * z^{n-1}, z^n (N_l - 1 each, may be NULL) in normalised units. */
 sfd_status sfd_string_state(const sfd_string* s, float* u_prev, float* u, float* z_prev, float* z);
+
+/* The state as the step kernel keeps it (Sec. 3.4's w^{n-1}, w^n in the
+ * increment form): u^n, D = u^n - u^{n-1} (N_t - 1 each), z^n and
+ * Dz = z^n - z^{n-1} (N_l - 1 each; zero without a longitudinal grid), FP32
+ * in normalised units, so that w^{n-1} = w^n - D is exact in FP64.  Any
+ * pointer may be NULL. */
+sfd_status sfd_string_delta_state(const sfd_string* s, float* u, float* du, float* z, float* dz);
+
+/* Hammer position u_H / L at time levels n-1 and n (Sec. 3.3.2, Eq. 6;
+ * FP32 as kept, widened).  SFD_EINVAL for a string not struck. */
+sfd_status sfd_string_hammer(const sfd_string* s, double* u_h_prev, double* u_h);
 
 /* Solver statistics of a string since creation: status (SFD_OK,
  * SFD_EUNSTABLE, SFD_ENOCONV), the largest and the total number of
@@ -240,6 +251,14 @@ sfd_status sfd_ctx_kernel_times(sfd_ctx* ctx, float* ms, int32_t* n_jobs);
  * scheduler.  The samples are bit for bit the same with and without groups.
  * enable = 0 steps every string with one warp. */
 sfd_status sfd_ctx_set_warp_pairs(sfd_ctx* ctx, int32_t enable);
+
+/* Sweep cap of the coupled transverse/longitudinal Gauss-Seidel solve for
+ * every later launch on this context (the joint solve of Sec. 3.4 is
+ * iterative; its tolerance is fixed, the cap bounds the work per step):
+ * 1..64, or 0 for the default 24.  A step that reaches the cap keeps its
+ * last iterate and marks the string SFD_ENOCONV; strings that need fewer
+ * sweeps give the same samples whatever the cap. */
+sfd_status sfd_ctx_set_sweep_cap(sfd_ctx* ctx, int32_t cap);
 
 /* Kernel class (0 .. SFD_KERNEL_CLASSES-1) a string runs in. */
 sfd_status sfd_string_kernel_class(const sfd_string* s, int32_t* cls);

@@ -138,6 +138,7 @@ struct sfd_ctx {
   int sm_count = 0;
   size_t smem_optin = 0;
   int warp_pairs = 1;                      // 0: every string on one warp (sfd_ctx_set_warp_pairs)
+  int sweep_cap = 0;                       // coupled-solve sweep cap of every launch (0: kMaxSweeps)
   Job* d_jobs = nullptr;
   int job_cap = 0;
   int* d_counter = nullptr;                // kClasses work-queue counters
@@ -677,7 +678,10 @@ sfd_status make_plan(const sfd_ctx* c, const std::vector<Job>& jobs, const std::
   P.jobs.assign(nj, Job{});
   for (int k = 0; k <= kClasses; ++k) P.first[k] = 0;
   for (int k = 0; k < kClasses; ++k) P.wf[k] = 0;
-  for (int i = 0; i < nj; ++i) P.jobs[i] = jobs[order[i]];
+  for (int i = 0; i < nj; ++i) {
+    P.jobs[i] = jobs[order[i]];
+    P.jobs[i].sweep_cap = c->sweep_cap;
+  }
   for (int i = 0; i < nj; ++i) {
     const int k = cls[order[i]];
     P.first[k + 1]++;
@@ -924,6 +928,14 @@ sfd_status sfd_grid(const sfd_string_params* p, int32_t* n_t, int32_t* n_l) {
   return SFD_OK;
 }
 
+sfd_status sfd_ctx_set_sweep_cap(sfd_ctx* c, int32_t cap) {
+  if (!c) return fail(SFD_EINVAL, "ctx is NULL");
+  if (cap < 0 || cap > kMaxSweepCap) return fail(SFD_EINVAL, "sweep cap must be 0 (default %d) or 1..%d", kMaxSweeps,
+                                                 kMaxSweepCap);
+  c->sweep_cap = cap;
+  return SFD_OK;
+}
+
 sfd_status sfd_modulation_peak(int32_t kind, double depth, double* ratio) {
   if (!ratio) return fail(SFD_EINVAL, "ratio is NULL");
   if (kind != SFD_MOD_NONE && kind != SFD_MOD_VIBRATO && kind != SFD_MOD_GLISS)
@@ -1116,8 +1128,8 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
   if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
   const double peak = std::isfinite(depth) ? modulation_peak(kind, depth) : 1.0;
   if (peak > s->p.f0_max_ratio * (1.0 + 1e-12)) {
-    // the grid grows to the modulation's peak: a new pool block for the
-    // larger state (nothing has run on the old one)
+    // the grid is re-derived for the modulation's peak (coarser: a faster
+    // wave), in a new pool block (nothing has run on the old one)
     if (s->batch_refs > 0)
       return fail(SFD_EBUSY, "the grid must grow to this modulation's peak: set it before adding the string to a batch");
     sfd_ctx* c = s->ctx;
@@ -1213,6 +1225,41 @@ sfd_status sfd_string_state(const sfd_string* s, float* u_prev, float* u, float*
     if (z) z[i] = zv;
     if (z_prev) z_prev[i] = zv - dzv;
   }
+  return SFD_OK;
+}
+
+sfd_status sfd_string_delta_state(const sfd_string* s, float* u, float* du, float* z, float* dz) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  if ((rc = flush_string(s))) return rc;
+  const Desc& D = s->h;
+  const int nz_full = s->n_l - 1;
+  sfd_ctx* c = s->ctx;
+  if (u) SFD_CUDA(d2h(c, u, D.u, sizeof(float) * D.n_u));
+  if (du) SFD_CUDA(d2h(c, du, D.du, sizeof(float) * D.n_u));
+  if (D.n_z > 0) {
+    if (z) SFD_CUDA(d2h(c, z, D.z, sizeof(float) * D.n_z));
+    if (dz) SFD_CUDA(d2h(c, dz, D.dz, sizeof(float) * D.n_z));
+  }
+  SFD_CUDA(cudaStreamSynchronize(c->stream));
+  for (int i = std::max(D.n_z, 0); i < nz_full; ++i) {   // no longitudinal grid: zero
+    if (z) z[i] = 0.f;
+    if (dz) dz[i] = 0.f;
+  }
+  return SFD_OK;
+}
+
+sfd_status sfd_string_hammer(const sfd_string* s, double* u_h_prev, double* u_h) {
+  if (!s) return fail(SFD_EINVAL, "string is NULL");
+  if (s->exc != kHammer) return fail(SFD_EINVAL, "the string is not struck by a hammer");
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  Scalars sc{};
+  if ((rc = flush_string(s))) return rc;
+  if ((rc = read_status(s, &sc))) return rc;
+  if (u_h) *u_h = sc.uh;
+  if (u_h_prev) *u_h_prev = static_cast<double>(sc.uh) - static_cast<double>(sc.duh);
   return SFD_OK;
 }
 

@@ -264,6 +264,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   const float bow_F = Dp->bow_F, bow_v = Dp->bow_v, bow_a = Dp->bow_a, bow_eps = Dp->bow_eps;
   const float kk = Dp->k, k2 = Dp->k2;
   const int64_t bow_release_n = Dp->bow_release_n;
+  const int sweep_cap = job.sweep_cap > 0 ? job.sweep_cap : kMaxSweeps;
 
   // ---- shared memory: transverse transfer arrays, then the longitudinal grid ----
   float* p = wbase;
@@ -754,7 +755,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           const float e = warp_max_nonneg(el);
           ++sweep;
           if (sweep_converged(e, e_prev, sweep)) break;
-          if (sweep >= kMaxSweeps) { status |= kStNoConv; break; }
+          if (sweep >= sweep_cap) { status |= kStNoConv; break; }
           e_prev = e;
         }
         sweeps_total += sweep;

@@ -34,6 +34,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   const float ca_0 = Dp->ca, cb_0 = Dp->cb, cz_0 = Dp->cz;
   const float bsgn = Dp->boundary == 1 ? -1.f : 1.f;
   const int mod_kind = Dp->mod_kind;
+  const int sweep_cap = job.sweep_cap > 0 ? job.sweep_cap : kMaxSweeps;
 
   // ---- carve the warp's shared-memory region (kArraysU + kArraysZ arrays) ----
   float* p = wbase;
@@ -370,7 +371,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
           ++sweep;
           const float e = fmaxf(chg > 0.f ? chg / mag : 0.f, chx > 0.f ? chx / mgx : 0.f);
           if (sweep_converged(e, e_prev, sweep)) break;
-          if (sweep >= kMaxSweeps) { status |= kStNoConv; break; }
+          if (sweep >= sweep_cap) { status |= kStNoConv; break; }
           e_prev = e;
         }
         sweeps_total += sweep;

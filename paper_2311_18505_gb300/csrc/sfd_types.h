@@ -8,7 +8,8 @@
 namespace sfd {
 
 constexpr int kWarp = 32;
-constexpr int kMaxSweeps = 24;       // cap of the coupled block Gauss-Seidel solve
+constexpr int kMaxSweeps = 24;       // default cap of the coupled block Gauss-Seidel solve
+constexpr int kMaxSweepCap = 64;     // largest cap a context may set
 constexpr float kSweepTol = 5e-7f;   // relative change that ends the solve
 
 enum ExcKind : int32_t { kPluck = 0, kHammer = 1, kBow = 2 };
@@ -100,6 +101,8 @@ struct Job {
   // for the job's k-th step; nullptr: not recorded
   float* traj;
   int64_t traj_stride;
+  int32_t sweep_cap;      // largest Gauss-Seidel sweep count per step (0: kMaxSweeps)
+  int32_t pad_;
 };
 
 // One string's part of a reverse sweep of the discrete adjoint over the

@@ -122,6 +122,9 @@ def lib() -> ctypes.CDLL:
         "sfd_string_state": (i32, [vp, vp, vp, vp, vp]),
         "sfd_string_destroy": (i32, [vp]),
         "sfd_string_stats": (i32, [vp, P(i32), P(i32), P(i64)]),
+        "sfd_string_delta_state": (i32, [vp, vp, vp, vp, vp]),
+        "sfd_string_hammer": (i32, [vp, P(dbl), P(dbl)]),
+        "sfd_ctx_set_sweep_cap": (i32, [vp, i32]),
         "sfd_batch_create": (i32, [vp, i32, P(vp), P(vp)]),
         "sfd_batch_synthesize": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
         "sfd_batch_synthesize_host": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
@@ -274,6 +277,22 @@ def sfd_string_state(s: int):
     return up, u, zp[: nl - 1], z[: nl - 1]
 
 
+def sfd_string_delta_state(s: int):
+    """(u^n, D, z^n, Dz) as the kernel keeps them (FP32, normalised)."""
+    nt, nl, _, _ = sfd_string_info(s)
+    u = np.zeros(nt - 1, np.float32); du = np.zeros(nt - 1, np.float32)
+    z = np.zeros(max(nl - 1, 1), np.float32); dz = np.zeros(max(nl - 1, 1), np.float32)
+    _check(lib().sfd_string_delta_state(s, u.ctypes.data, du.ctypes.data, z.ctypes.data, dz.ctypes.data))
+    return u, du, z[: nl - 1], dz[: nl - 1]
+
+
+def sfd_string_hammer(s: int) -> tuple[float, float]:
+    """Hammer position u_H / L at levels n-1 and n."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sfd_string_hammer(s, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def sfd_string_stats(s: int) -> tuple[int, int, int]:
     """(status, max sweeps, total sweeps) of the coupled solve."""
     st, mx, tot = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
@@ -374,6 +393,10 @@ def sfd_ctx_set_timing(ctx: int, enable: bool) -> None:
 
 def sfd_ctx_set_warp_pairs(ctx: int, enable: bool) -> None:
     _check(lib().sfd_ctx_set_warp_pairs(ctx, 1 if enable else 0))
+
+
+def sfd_ctx_set_sweep_cap(ctx: int, cap: int) -> None:
+    _check(lib().sfd_ctx_set_sweep_cap(ctx, cap))
 
 
 def sfd_ctx_kernel_times(ctx: int):

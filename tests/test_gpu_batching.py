@@ -252,7 +252,8 @@ def test_warp_pairs_change_nothing(sfd):
 
 def test_modulation_grows_the_grid_before_the_first_synthesis(sfd):
     """A string created without room for its modulation's peak (f0_max_ratio
-    1) gets the grid of that peak from sfd_set_modulation (reading A14), with
+    1, a grid too fine to be stable at the peak wave speed) gets the grid of
+    that peak from sfd_set_modulation (reading A14), with
     its hammer at the same position: grid and samples equal a string sized
     for the peak at creation, bit for bit.  In a batch the grid can no
     longer change (SFD_EBUSY)."""
@@ -267,7 +268,7 @@ def test_modulation_grows_the_grid_before_the_first_synthesis(sfd):
         small = sfd.sfd_string_info(late)[:2]
         sfd.sfd_set_modulation(late, sfd.SFD_MOD_GLISS, 0.0, 1.0, 0.0, 0.0625)
         assert sfd.sfd_string_info(late)[:2] == sfd.sfd_string_info(sized)[:2] == sfd.sfd_grid(sfd.params_from_dict(d))
-        assert sfd.sfd_string_info(late)[0] > small[0]
+        assert sfd.sfd_string_info(late)[0] < small[0]   # a faster peak wave: a coarser grid
         assert np.array_equal(sfd.sfd_synthesize(late, 3000), sfd.sfd_synthesize(sized, 3000))
         sfd.sfd_string_destroy(late)
         sfd.sfd_string_destroy(sized)
