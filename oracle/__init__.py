@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfd_oracle.c")
 _HDR = os.path.join(_HERE, "sfd_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "libsfd_oracle.so")
+_OUT_CS = os.path.join(_HERE, "_build", "libsfd_oracle_cs.so")
 
 EXC = {"pluck": 0, "hammer": 1, "bow": 2}
 MOD = {"none": 0, "vibrato": 1, "gliss": 2}
@@ -65,7 +66,62 @@ def build(force: bool = False) -> str:
     return _OUT
 
 
+def build_cs(force: bool = False) -> str:
+    """Compile the same source a second time with a complex scalar
+    (-DSFDO_COMPLEX): the complex-step derivative library."""
+    os.makedirs(os.path.dirname(_OUT_CS), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_OUT_CS) or os.path.getmtime(_OUT_CS) < newest:
+        tmp = _OUT_CS + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-DSFDO_COMPLEX",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _OUT_CS)
+    return _OUT_CS
+
+
 _lib = None
+_lib_cs = None
+
+
+def lib_cs():
+    global _lib_cs
+    if _lib_cs is None:
+        L = ctypes.CDLL(build_cs())
+        P = ctypes.POINTER
+        L.sfdo_cs_run.argtypes = [P(Spec), ctypes.c_int, ctypes.c_double, ctypes.c_int64, P(ctypes.c_double),
+                                  P(ctypes.c_double)]
+        L.sfdo_cs_run.restype = ctypes.c_int
+        _lib_cs = L
+    return _lib_cs
+
+
+GRAD_PARAMS = ("kappa", "alpha", "sigma0", "sigma1", "amplitude")
+
+
+def complex_step(d: dict, which: int, n: int | None = None, h: float = 1e-30, n_t: int = 0, n_l: int = 0):
+    """(y, dy/dp) of one string for parameter GRAD_PARAMS[which] by the
+    complex step (exact to rounding on a smooth path).  The grid is held at
+    the parameters' own grid (or n_t, n_l)."""
+    n = d["n_samples"] if n is None else n
+    if not (n_t and n_l):
+        n_t, n_l = grid(d)
+    sp = spec(d, n_t, n_l)
+    y = np.zeros(n)
+    dy = np.zeros(n)
+    rc = lib_cs().sfdo_cs_run(ctypes.byref(sp), which, h, n, _ptr(y), _ptr(dy))
+    if rc != 0:
+        raise FloatingPointError(f"complex-step run failed (code {rc})")
+    return y, dy
+
+
+def loss_gradient_cs(d: dict, target: np.ndarray, n: int | None = None) -> np.ndarray:
+    """Gradient of J = sum (y - target)^2 with respect to GRAD_PARAMS by the
+    complex step, on the string's own grid."""
+    g = np.zeros(len(GRAD_PARAMS))
+    for w in range(len(GRAD_PARAMS)):
+        y, dy = complex_step(d, w, n)
+        g[w] = float(np.sum(2.0 * (y - target[: len(y)]) * dy))
+    return g
 
 
 def lib():

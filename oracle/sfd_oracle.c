@@ -22,24 +22,49 @@
 
 #define PI_D 3.14159265358979323846
 
+/* The scalar of the state, the system and the differentiable parameters.
+ * Built a second time with -DSFDO_COMPLEX it is a complex double: a
+ * parameter given an imaginary part i h then carries its derivative along
+ * every operation (complex step: dy/dp = Im y / h, exact to rounding for a
+ * smooth path).  Branches test real parts; |x| is continued analytically as
+ * sign(Re x) x.  With plain doubles the macros are the usual functions. */
+#ifdef SFDO_COMPLEX
+#include <complex.h>
+typedef double complex num_t;
+#define RE(x) creal(x)
+#define NEXP(x) cexp(x)
+#define NPOW(x, y) cpow((x), (y))
+#define NABS(x) (creal(x) < 0 ? -(x) : (x))
+#define NMAG(x) cabs(x)
+#else
+typedef double num_t;
+#define RE(x) (x)
+#define NEXP(x) exp(x)
+#define NPOW(x, y) pow((x), (y))
+#define NABS(x) fabs(x)
+#define NMAG(x) fabs(x)
+#endif
+
 struct sfdo_string {
   sfdo_spec p;
   int nt, nl;            /* intervals N_t, N_l (Sec. 3, Eq. 3 notation)      */
   int nu, nz;            /* unknowns N_t-1, N_l-1 (Sec. 3.4)                 */
   double ht, hl, k;      /* spacings and time step                           */
-  double *u, *up;        /* u^n, u^{n-1}, index l-1 for node l               */
-  double *z, *zp;        /* z^n, z^{n-1}, index m-1 for node m               */
-  double uh, uhp;        /* hammer u_H^n, u_H^{n-1} (Eq. 6)                  */
+  num_t kappa, alpha, sigma0, sigma1;   /* the differentiable parameters     */
+  num_t amp;             /* pluck amplitude, hammer or bow velocity           */
+  num_t *u, *up;         /* u^n, u^{n-1}, index l-1 for node l               */
+  num_t *z, *zp;         /* z^n, z^{n-1}, index m-1 for node m               */
+  num_t uh, uhp;         /* hammer u_H^n, u_H^{n-1} (Eq. 6)                  */
   int64_t n;             /* time level: state holds w^{n-1}, w^n             */
   int64_t next_out;      /* index of the next output sample                  */
   /* linear system, position ordered */
   int ntot, hrow, bw, pattern;
   int *urow, *zrow;      /* node -> row, -1 at the fixed ends                */
-  double *band, *band0, *rhs, *sol, *rhs0;
-  double *zsol;          /* second solution (unit force) for the bow         */
-  double *tmp, *tmpx;    /* residual workspace                               */
+  num_t *band, *band0, *rhs, *sol, *rhs0;
+  num_t *zsol;           /* second solution (unit force) for the bow         */
+  num_t *tmp, *tmpx;     /* residual workspace                               */
   /* interval quantities, index 1..N (entry 0 unused)                        */
-  double *q, *qp, *pt, *ptp;
+  num_t *q, *qp, *pt, *ptp;
   /* overlap weights R_ij = |T_i cap L_j| / h_t, both directions (A6)      */
   int *t_ptr, *t_j; double *t_w;   /* for t-interval i: list of (j, R_ij)   */
   int *l_ptr, *l_i; double *l_w;   /* for l-interval j: list of (i, R_ij)   */
@@ -47,7 +72,8 @@ struct sfdo_string {
   int e_node[2]; double e_w[2];
   int o_node[2]; double o_w[2];
   int ol_node[2]; double ol_w[2];   /* pickup on the longitudinal grid */
-  double last_power, last_G, last_v, last_F, last_resid;
+  num_t last_power, last_G, last_v, last_F;
+  double last_resid;
 };
 
 /* ------------------------------------------------------------------ grid */
@@ -89,13 +115,13 @@ int sfdo_grid(const sfdo_spec* s, int32_t* n_t, int32_t* n_l) {
 
 /* ------------------------------------------------------------ helpers */
 
-static double U(const sfdo_string* S, const double* u, int l) {
+static num_t U(const sfdo_string* S, const num_t* u, int l) {
   /* node value with the fixed ends u_0 = u_N = 0 (Sec. 3.4: N-1 unknowns) */
   if (l <= 0 || l >= S->nt) return 0.0;
   return u[l - 1];
 }
 
-static double Ughost(const sfdo_string* S, const double* u, int l) {
+static num_t Ughost(const sfdo_string* S, const num_t* u, int l) {
   /* ghost nodes for the fourth difference: clamped u_{-1} = u_1,
    * simply supported u_{-1} = -u_1 (and mirrored at x = 1). */
   const double sgn = S->p.boundary == 1 ? -1.0 : 1.0;
@@ -104,24 +130,24 @@ static double Ughost(const sfdo_string* S, const double* u, int l) {
   return U(S, u, l);
 }
 
-static double Z(const sfdo_string* S, const double* z, int m) {
+static num_t Z(const sfdo_string* S, const num_t* z, int m) {
   if (m <= 0 || m >= S->nl) return 0.0;
   return z[m - 1];
 }
 
 /* delta_xx u at node l (Sec. 3.1) */
-static double dxx(const sfdo_string* S, const double* u, int l) {
+static num_t dxx(const sfdo_string* S, const num_t* u, int l) {
   return (U(S, u, l + 1) - 2.0 * U(S, u, l) + U(S, u, l - 1)) / (S->ht * S->ht);
 }
 
 /* delta_xxxx u at node l with the boundary ghosts (Sec. 3.2) */
-static double dxxxx(const sfdo_string* S, const double* u, int l) {
+static num_t dxxxx(const sfdo_string* S, const num_t* u, int l) {
   const double h4 = S->ht * S->ht * S->ht * S->ht;
   return (Ughost(S, u, l + 2) - 4.0 * Ughost(S, u, l + 1) + 6.0 * Ughost(S, u, l) -
           4.0 * Ughost(S, u, l - 1) + Ughost(S, u, l - 2)) / h4;
 }
 
-static double dzz(const sfdo_string* S, const double* z, int m) {
+static num_t dzz(const sfdo_string* S, const num_t* z, int m) {
   return (Z(S, z, m + 1) - 2.0 * Z(S, z, m) + Z(S, z, m - 1)) / (S->hl * S->hl);
 }
 
@@ -136,7 +162,7 @@ static void interp_weights(const sfdo_string* S, double x, int node[2], double w
   node[1] = l + 1; w[1] = a;
 }
 
-static double interp(const sfdo_string* S, const double* u, const int node[2], const double w[2]) {
+static num_t interp(const sfdo_string* S, const num_t* u, const int node[2], const double w[2]) {
   return w[0] * U(S, u, node[0]) + w[1] * U(S, u, node[1]);
 }
 
@@ -175,7 +201,7 @@ static double gamma_at(const sfdo_string* S, int64_t n) {
 
 /* ------------------------------------------------------- band storage */
 
-static void add(sfdo_string* S, int r, int c, double v) {
+static void add(sfdo_string* S, int r, int c, num_t v) {
   if (r < 0 || c < 0) return;
   if (S->pattern) {
     int d = abs(r - c);
@@ -189,36 +215,36 @@ static void add(sfdo_string* S, int r, int c, double v) {
  * by h_t and the z rows by h_l the matrix of Eqs. 7-8 is symmetric positive
  * definite (the coupling blocks are adjoint, A6), so all leading minors are
  * positive and no pivoting is needed. */
-static int band_solve(sfdo_string* S, double* b) {
+static int band_solve(sfdo_string* S, num_t* b) {
   const int n = S->ntot, bw = S->bw, ld = 2 * bw + 1;
-  double* A = S->band;
+  num_t* A = S->band;
   for (int kk = 0; kk < n; ++kk) {
-    const double piv = A[(size_t)kk * ld + bw];
-    if (piv == 0.0 || !isfinite(piv)) return -4;
+    const num_t piv = A[(size_t)kk * ld + bw];
+    if (piv == 0.0 || !isfinite(RE(piv))) return -4;
     const int iend = kk + bw < n - 1 ? kk + bw : n - 1;
     for (int i = kk + 1; i <= iend; ++i) {
-      double* ai = A + (size_t)i * ld;
-      const double l = ai[kk - i + bw] / piv;
+      num_t* ai = A + (size_t)i * ld;
+      const num_t l = ai[kk - i + bw] / piv;
       if (l == 0.0) continue;
       ai[kk - i + bw] = l;
-      const double* ak = A + (size_t)kk * ld;
+      const num_t* ak = A + (size_t)kk * ld;
       for (int j = kk + 1; j <= kk + bw && j < n; ++j) ai[j - i + bw] -= l * ak[j - kk + bw];
       b[i] -= l * b[kk];
     }
   }
   for (int i = n - 1; i >= 0; --i) {
-    const double* ai = A + (size_t)i * ld;
-    double s = b[i];
+    const num_t* ai = A + (size_t)i * ld;
+    num_t s = b[i];
     for (int j = i + 1; j <= i + bw && j < n; ++j) s -= ai[j - i + bw] * b[j];
     b[i] = s / ai[bw];
   }
   return 0;
 }
 
-static void band_mul(const sfdo_string* S, const double* A, const double* x, double* y) {
+static void band_mul(const sfdo_string* S, const num_t* A, const num_t* x, num_t* y) {
   const int n = S->ntot, bw = S->bw, ld = 2 * bw + 1;
   for (int i = 0; i < n; ++i) {
-    double s = 0;
+    num_t s = 0;
     for (int j = i - bw; j <= i + bw; ++j)
       if (j >= 0 && j < n) s += A[(size_t)i * ld + (j - i + bw)] * x[j];
     y[i] = s;
@@ -312,9 +338,12 @@ static void build_ordering(sfdo_string* S) {
   free(v);
 }
 
-static void assemble(sfdo_string* S, double gam, double hamG);
+static void assemble(sfdo_string* S, double gam, num_t hamG);
 
-sfdo_string* sfdo_create(const sfdo_spec* s) {
+/* A string at time level 1; `which` >= 0 (complex build only) gives that
+ * parameter (0 kappa, 1 alpha, 2 sigma0, 3 sigma1, 4 the pluck amplitude,
+ * hammer velocity or bow velocity) the imaginary part h. */
+static sfdo_string* create_string(const sfdo_spec* s, int which, double h) {
   int32_t nt, nl;
   if (sfdo_grid(s, &nt, &nl) != 0) return NULL;
   if (!(s->pickup > 0 && s->pickup < 1) || !(s->length > 0) || !(s->rho_a > 0)) return NULL;
@@ -337,14 +366,22 @@ sfdo_string* sfdo_create(const sfdo_spec* s) {
   S->nt = nt; S->nl = nl;
   S->nu = nt - 1; S->nz = nl > 1 ? nl - 1 : 0;
   S->ht = 1.0 / nt; S->hl = 1.0 / nl; S->k = 1.0 / s->fs;
-  S->u = calloc(S->nu + 1, sizeof(double));
-  S->up = calloc(S->nu + 1, sizeof(double));
-  S->z = calloc(S->nz + 1, sizeof(double));
-  S->zp = calloc(S->nz + 1, sizeof(double));
-  S->q = calloc(nt + 2, sizeof(double));
-  S->qp = calloc(nt + 2, sizeof(double));
-  S->pt = calloc(nt + 2, sizeof(double));
-  S->ptp = calloc(nt + 2, sizeof(double));
+  S->kappa = s->kappa; S->alpha = s->alpha; S->sigma0 = s->sigma0; S->sigma1 = s->sigma1;
+  S->amp = s->exc_kind == SFDO_EXC_PLUCK ? s->pluck_amp : (s->exc_kind == SFDO_EXC_HAMMER ? s->ham_vel : s->bow_vel);
+#ifdef SFDO_COMPLEX
+  num_t* pick[5] = {&S->kappa, &S->alpha, &S->sigma0, &S->sigma1, &S->amp};
+  if (which >= 0 && which < 5) *pick[which] += I * h;
+#else
+  (void)which; (void)h;
+#endif
+  S->u = calloc(S->nu + 1, sizeof(num_t));
+  S->up = calloc(S->nu + 1, sizeof(num_t));
+  S->z = calloc(S->nz + 1, sizeof(num_t));
+  S->zp = calloc(S->nz + 1, sizeof(num_t));
+  S->q = calloc(nt + 2, sizeof(num_t));
+  S->qp = calloc(nt + 2, sizeof(num_t));
+  S->pt = calloc(nt + 2, sizeof(num_t));
+  S->ptp = calloc(nt + 2, sizeof(num_t));
   build_overlaps(S);
   build_ordering(S);
   interp_weights(S, s->pickup, S->o_node, S->o_w);
@@ -366,33 +403,36 @@ sfdo_string* sfdo_create(const sfdo_spec* s) {
   S->pattern = 0;
   if (S->bw < 1) S->bw = 1;
   const size_t bsz = (size_t)(S->ntot > 0 ? S->ntot : 1) * (2 * S->bw + 1);
-  S->band = calloc(bsz, sizeof(double));
-  S->band0 = calloc(bsz, sizeof(double));
-  S->rhs = calloc(S->ntot + 1, sizeof(double));
-  S->rhs0 = calloc(S->ntot + 1, sizeof(double));
-  S->sol = calloc(S->ntot + 1, sizeof(double));
-  S->zsol = calloc(S->ntot + 1, sizeof(double));
-  S->tmp = calloc(S->ntot + 1, sizeof(double));
-  S->tmpx = calloc(S->ntot + 1, sizeof(double));
-  memset(S->q, 0, sizeof(double) * (nt + 2));
+  S->band = calloc(bsz, sizeof(num_t));
+  S->band0 = calloc(bsz, sizeof(num_t));
+  S->rhs = calloc(S->ntot + 1, sizeof(num_t));
+  S->rhs0 = calloc(S->ntot + 1, sizeof(num_t));
+  S->sol = calloc(S->ntot + 1, sizeof(num_t));
+  S->zsol = calloc(S->ntot + 1, sizeof(num_t));
+  S->tmp = calloc(S->ntot + 1, sizeof(num_t));
+  S->tmpx = calloc(S->ntot + 1, sizeof(num_t));
+  memset(S->q, 0, sizeof(num_t) * (nt + 2));
   /* initial conditions w^0, w^1 (Sec. 3.3 and 3.4) */
   if (s->exc_kind == SFDO_EXC_PLUCK) {
     /* triangle with peak c0 = amp/L at x_P, zero initial velocity (A9) */
-    const double c0 = s->pluck_amp / s->length, xp = s->pluck_pos;
+    const num_t c0 = S->amp / s->length;
+    const double xp = s->pluck_pos;
     for (int l = 1; l < nt; ++l) {
       const double x = (double)l / nt;
-      const double v = x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp);
+      const num_t v = x <= xp ? c0 * x / xp : c0 * (1.0 - x) / (1.0 - xp);
       S->u[l - 1] = v; S->up[l - 1] = v;
     }
   } else if (s->exc_kind == SFDO_EXC_HAMMER) {
     /* hammer starts at the string with velocity v_H: u_H^0 = 0, u_H^1 = v_H k */
     S->uhp = 0.0;
-    S->uh = (s->ham_vel / s->length) * S->k;
+    S->uh = (S->amp / s->length) * S->k;
   }
   S->n = 1;
   S->next_out = 0;
   return S;
 }
+
+sfdo_string* sfdo_create(const sfdo_spec* s) { return create_string(s, -1, 0.0); }
 
 void sfdo_destroy(sfdo_string* S) {
   if (!S) return;
@@ -413,20 +453,20 @@ void sfdo_destroy(sfdo_string* S) {
  *   Theta = theta I + (1-theta) M_x. (Sec. 3.2),
  * mu_t. q = (q^{n+1}+q^{n-1})/2 and mu_tt p = (p^{n+1}+2p^n+p^{n-1})/4.
  * hamG is the hammer stiffness coefficient of Eq. 6 (0 without contact). */
-static void assemble(sfdo_string* S, double gam, double hamG) {
+static void assemble(sfdo_string* S, double gam, num_t hamG) {
   const sfdo_spec* P = &S->p;
   const int nt = S->nt, nl = S->nl;
   const double k = S->k, ht = S->ht, hl = S->hl;
   const double th = P->theta;
   const double g2k2 = gam * gam * k * k;
-  const double kk2 = P->kappa * P->kappa * k * k;
-  const double s0k = P->sigma0 * k, s1k = P->sigma1 * k;
-  const double cnl = 0.5 * gam * gam * (P->alpha * P->alpha - 1.0) * k * k; /* phi' k^2 */
-  const double* q = S->q;
+  const num_t kk2 = S->kappa * S->kappa * k * k;
+  const num_t s0k = S->sigma0 * k, s1k = S->sigma1 * k;
+  const num_t cnl = 0.5 * gam * gam * (S->alpha * S->alpha - 1.0) * k * k; /* phi' k^2 */
+  const num_t* q = S->q;
 
   if (!S->pattern) {
-    memset(S->band, 0, sizeof(double) * (size_t)S->ntot * (2 * S->bw + 1));
-    memset(S->rhs, 0, sizeof(double) * S->ntot);
+    memset(S->band, 0, sizeof(num_t) * (size_t)S->ntot * (2 * S->bw + 1));
+    memset(S->rhs, 0, sizeof(num_t) * S->ntot);
   }
 
   /* ---- transverse rows, Eq. 4 (first line) ---- */
@@ -440,20 +480,20 @@ static void assemble(sfdo_string* S, double gam, double hamG) {
     for (int side = 0; side < 2; ++side) {
       const int i = side == 0 ? l : l + 1;          /* intervals l and l+1 */
       const double sg = side == 0 ? 1.0 : -1.0;
-      const double coef = sg * cnl / (2.0 * ht);
+      const num_t coef = sg * cnl / (2.0 * ht);
       add(S, r, S->urow[i], coef * q[i] * q[i] / ht);
       add(S, r, S->urow[i - 1], -coef * q[i] * q[i] / ht);
       for (int e = S->t_ptr[i]; e < S->t_ptr[i + 1]; ++e) {
         const int j = S->t_j[e];
-        const double w = coef * q[i] * S->t_w[e] / hl;
+        const num_t w = coef * q[i] * S->t_w[e] / hl;
         add(S, r, S->zrow[j], w);
         add(S, r, S->zrow[j - 1], -w);
       }
     }
     if (S->pattern) continue;
-    const double* u = S->u;
-    const double* up = S->up;
-    double b = th * (2.0 * U(S, u, l) - U(S, up, l)) +
+    const num_t* u = S->u;
+    const num_t* up = S->up;
+    num_t b = th * (2.0 * U(S, u, l) - U(S, up, l)) +
                0.5 * (1.0 - th) * (2.0 * U(S, u, l - 1) - U(S, up, l - 1) + 2.0 * U(S, u, l + 1) - U(S, up, l + 1));
     b += g2k2 * dxx(S, u, l);
     b -= kk2 * dxxxx(S, u, l);
@@ -462,8 +502,8 @@ static void assemble(sfdo_string* S, double gam, double hamG) {
     /* (phi'k^2/2) delta_x+ [ q^2 q^{n-1} + q (2 ptilde^n + ptilde^{n-1}) ] */
     {
       const int i1 = l + 1, i0 = l;
-      const double y1 = q[i1] * q[i1] * S->qp[i1] + q[i1] * (2.0 * S->pt[i1] + S->ptp[i1]);
-      const double y0 = q[i0] * q[i0] * S->qp[i0] + q[i0] * (2.0 * S->pt[i0] + S->ptp[i0]);
+      const num_t y1 = q[i1] * q[i1] * S->qp[i1] + q[i1] * (2.0 * S->pt[i1] + S->ptp[i1]);
+      const num_t y0 = q[i0] * q[i0] * S->qp[i0] + q[i0] * (2.0 * S->pt[i0] + S->ptp[i0]);
       b += cnl / (2.0 * ht) * (y1 - y0);
     }
     S->rhs[r] = b;
@@ -479,22 +519,22 @@ static void assemble(sfdo_string* S, double gam, double hamG) {
     for (int side = 0; side < 2; ++side) {
       const int j = side == 0 ? m : m + 1;
       const double sg = side == 0 ? 1.0 : -1.0;
-      const double coef = sg * cnl / (2.0 * hl) * (ht / hl);
+      const num_t coef = sg * cnl / (2.0 * hl) * (ht / hl);
       for (int e = S->l_ptr[j]; e < S->l_ptr[j + 1]; ++e) {
         const int i = S->l_i[e];
-        const double w = coef * S->l_w[e] * q[i] / ht;
+        const num_t w = coef * S->l_w[e] * q[i] / ht;
         add(S, r, S->urow[i], w);
         add(S, r, S->urow[i - 1], -w);
       }
     }
     if (S->pattern) continue;
-    const double* z = S->z;
-    const double* zp = S->zp;
-    double b = 2.0 * Z(S, z, m) - Z(S, zp, m);
-    b += g2k2 * P->alpha * P->alpha * dzz(S, z, m);
+    const num_t* z = S->z;
+    const num_t* zp = S->zp;
+    num_t b = 2.0 * Z(S, z, m) - Z(S, zp, m);
+    b += g2k2 * S->alpha * S->alpha * dzz(S, z, m);
     b += s0k * Z(S, zp, m);
     b -= s1k * dzz(S, zp, m);
-    double sz1 = 0, sz0 = 0;   /* (S [q q^{n-1}])_{m+1}, (S [q q^{n-1}])_m */
+    num_t sz1 = 0, sz0 = 0;   /* (S [q q^{n-1}])_{m+1}, (S [q q^{n-1}])_m */
     for (int e = S->l_ptr[m + 1]; e < S->l_ptr[m + 2]; ++e) {
       const int i = S->l_i[e];
       sz1 += S->l_w[e] * q[i] * S->qp[i];
@@ -513,9 +553,9 @@ static void assemble(sfdo_string* S, double gam, double hamG) {
    * solved jointly here as one extra unknown.  M = m_H / (rho A L). ---- */
   if (P->exc_kind == SFDO_EXC_HAMMER) {
     const double M = P->ham_mass / (P->rho_a * P->length);
-    const double cg = 0.5 * k * k * hamG;
+    const num_t cg = 0.5 * k * k * hamG;
     const int hr = S->hrow;
-    double etap = 0.0;
+    num_t etap = 0.0;
     if (!S->pattern) etap = S->uhp - interp(S, S->up, S->e_node, S->e_w);
     for (int a = 0; a < 2; ++a) {
       const int la = S->e_node[a];
@@ -542,25 +582,27 @@ static void assemble(sfdo_string* S, double gam, double hamG) {
 
 /* Bow friction characteristic of Sec. 3.3.1 with the argument read as the
  * relative velocity (reading A11): phi(v) = sign(v)(eps + (1-eps)e^{-a|v|}). */
-static double friction_mag(double a, double eps, double w) { return eps + (1.0 - eps) * exp(-a * w); }
+static num_t friction_mag(double a, double eps, num_t w) { return eps + (1.0 - eps) * NEXP(-a * w); }
 
 /* Solve v + c phi(v) = b (Eq. 5 after eliminating u^{n+1}; reading A11):
  * |b| <= c -> sticking, v = 0 and phi = b/c; otherwise the unique root of
  * the convex g(w) = w + c phi(w) - |b| on (0, |b|) with sign(v) = sign(b),
  * found by Newton from w = |b| guarded by bisection. Returns phi(v). */
-static double bow_solve(double b, double c, double a, double eps, double* v_out) {
-  if (!(c > 0)) { *v_out = b; return b == 0 ? 0.0 : (b > 0 ? 1.0 : -1.0) * friction_mag(a, eps, fabs(b)); }
-  if (fabs(b) <= c) { *v_out = 0.0; return b / c; }
-  const double B = fabs(b), sg = b > 0 ? 1.0 : -1.0;
-  double lo = 0.0, hi = B, w = B;
+static num_t bow_solve(num_t b, num_t c, double a, double eps, num_t* v_out) {
+  if (!(RE(c) > 0)) { *v_out = b; return b == 0 ? 0.0 : (RE(b) > 0 ? 1.0 : -1.0) * friction_mag(a, eps, NABS(b)); }
+  if (RE(NABS(b)) <= RE(c)) { *v_out = 0.0; return b / c; }
+  const num_t B = NABS(b);
+  const double sg = RE(b) > 0 ? 1.0 : -1.0;
+  double lo = 0.0, hi = RE(B);
+  num_t w = B;
   for (int it = 0; it < 200; ++it) {
-    const double e = exp(-a * w);
-    const double g = w + c * (eps + (1.0 - eps) * e) - B;
-    if (g > 0) hi = w; else lo = w;
-    const double dg = 1.0 - c * (1.0 - eps) * a * e;
-    double wn = dg > 0 ? w - g / dg : 0.5 * (lo + hi);
-    if (!(wn > lo && wn < hi)) wn = 0.5 * (lo + hi);
-    if (fabs(wn - w) <= 1e-16 * (1.0 + w)) { w = wn; break; }
+    const num_t e = NEXP(-a * w);
+    const num_t g = w + c * (eps + (1.0 - eps) * e) - B;
+    if (RE(g) > 0) hi = RE(w); else lo = RE(w);
+    const num_t dg = 1.0 - c * (1.0 - eps) * a * e;
+    num_t wn = RE(dg) > 0 ? w - g / dg : 0.5 * (lo + hi);
+    if (!(RE(wn) > lo && RE(wn) < hi)) wn = 0.5 * (lo + hi);
+    if (NMAG(wn - w) <= 1e-16 * (1.0 + RE(w))) { w = wn; break; }
     w = wn;
   }
   *v_out = sg * w;
@@ -576,7 +618,7 @@ static int step(sfdo_string* S) {
   for (int i = 1; i <= nt; ++i) {
     S->q[i] = (U(S, S->u, i) - U(S, S->u, i - 1)) / S->ht;
     S->qp[i] = (U(S, S->up, i) - U(S, S->up, i - 1)) / S->ht;
-    double s = 0, sp = 0;
+    num_t s = 0, sp = 0;
     for (int e = S->t_ptr[i]; e < S->t_ptr[i + 1]; ++e) {
       const int j = S->t_j[e];
       s += S->t_w[e] * (Z(S, S->z, j) - Z(S, S->z, j - 1)) / S->hl;
@@ -584,32 +626,35 @@ static int step(sfdo_string* S) {
     }
     S->pt[i] = s; S->ptp[i] = sp;
   }
-  double hamG = 0.0;
+  num_t hamG = 0.0;
   if (P->exc_kind == SFDO_EXC_HAMMER) {
-    const double eta = S->uh - interp(S, S->u, S->e_node, S->e_w);
-    hamG = eta > 0 ? pow(P->ham_omega, 1.0 + P->ham_alpha) * pow(eta, P->ham_alpha - 1.0) : 0.0;
+    const num_t eta = S->uh - interp(S, S->u, S->e_node, S->e_w);
+    hamG = RE(eta) > 0 ? pow(P->ham_omega, 1.0 + P->ham_alpha) * NPOW(eta, P->ham_alpha - 1.0) : 0.0;
   }
   assemble(S, gam, hamG);
   const size_t bsz = (size_t)S->ntot * (2 * S->bw + 1);
-  memcpy(S->band0, S->band, sizeof(double) * bsz);
-  memcpy(S->rhs0, S->rhs, sizeof(double) * S->ntot);
-  memcpy(S->sol, S->rhs, sizeof(double) * S->ntot);
+  memcpy(S->band0, S->band, sizeof(num_t) * bsz);
+  memcpy(S->rhs0, S->rhs, sizeof(num_t) * S->ntot);
+  memcpy(S->sol, S->rhs, sizeof(num_t) * S->ntot);
   int rc = band_solve(S, S->sol);   /* band now holds the LU factors */
   if (rc) return rc;
-  double force = 0.0;               /* normalised force on the string      */
+  num_t force = 0.0;                /* normalised force on the string      */
   if (P->exc_kind == SFDO_EXC_BOW) {
     const double t = (double)S->n * k;
-    double bv = P->bow_vel, bf = P->bow_force;
+    num_t bv = S->amp;
+    double bf = P->bow_force;
     if (P->bow_env_n > 0) {   /* time-varying controls: the step's values, and I, J at x_B(t) */
-      double bx = P->bow_pos;
-      bow_controls(P, t, &bv, &bf, &bx);
+      double bx = P->bow_pos, ev = 0.0;
+      bow_controls(P, t, &ev, &bf, &bx);
+      bv = ev;
       interp_weights(S, bx, S->e_node, S->e_w);
     }
     const double FB = (P->bow_release >= 0 && t >= P->bow_release) ? 0.0
                       : bf / (P->rho_a * P->length * P->length);
-    const double vB = bv / P->length, aN = P->bow_a * P->length;
+    const num_t vB = bv / P->length;
+    const double aN = P->bow_a * P->length;
     /* unit-force response A z = J (same factors) */
-    memset(S->zsol, 0, sizeof(double) * S->ntot);
+    memset(S->zsol, 0, sizeof(num_t) * S->ntot);
     for (int a = 0; a < 2; ++a) {
       const int la = S->e_node[a];
       if (la > 0 && la < nt) S->zsol[S->urow[la]] += S->e_w[a] / S->ht;
@@ -617,17 +662,17 @@ static int step(sfdo_string* S) {
     /* re-solve with the stored LU factors: forward (unit lower) + backward */
     {
       const int n = S->ntot, bw = S->bw, ld = 2 * bw + 1;
-      const double* A = S->band;
-      double* x = S->zsol;
+      const num_t* A = S->band;
+      num_t* x = S->zsol;
       for (int kk = 0; kk < n; ++kk)
         for (int i = kk + 1; i <= kk + bw && i < n; ++i) x[i] -= A[(size_t)i * ld + (kk - i + bw)] * x[kk];
       for (int i = n - 1; i >= 0; --i) {
-        double s = x[i];
+        num_t s = x[i];
         for (int j = i + 1; j <= i + bw && j < n; ++j) s -= A[(size_t)i * ld + (j - i + bw)] * x[j];
         x[i] = s / A[(size_t)i * ld + bw];
       }
     }
-    double Iu = 0, Iz = 0, Iup = 0;
+    num_t Iu = 0, Iz = 0, Iup = 0;
     for (int a = 0; a < 2; ++a) {
       const int la = S->e_node[a];
       if (la <= 0 || la >= nt) continue;
@@ -635,10 +680,10 @@ static int step(sfdo_string* S) {
       Iz += S->e_w[a] * S->zsol[S->urow[la]];
       Iup += S->e_w[a] * S->up[la - 1];
     }
-    const double b = (Iu - Iup) / (2.0 * k) - vB;
-    const double c = 0.5 * k * FB * Iz;
-    double v;
-    const double ph = bow_solve(b, c, aN, P->bow_eps, &v);
+    const num_t b = (Iu - Iup) / (2.0 * k) - vB;
+    const num_t c = 0.5 * k * FB * Iz;
+    num_t v;
+    const num_t ph = bow_solve(b, c, aN, P->bow_eps, &v);
     force = -FB * ph;
     for (int r = 0; r < S->ntot; ++r) S->sol[r] += k * k * force * S->zsol[r];
     S->last_v = v;
@@ -646,21 +691,21 @@ static int step(sfdo_string* S) {
   /* residual of the assembled system (without the bow term, which is added
    * through the exact unit-force response) */
   {
-    double* tmp = S->tmp;
-    double* x = S->tmpx;
-    memcpy(x, S->sol, sizeof(double) * S->ntot);
+    num_t* tmp = S->tmp;
+    num_t* x = S->tmpx;
+    memcpy(x, S->sol, sizeof(num_t) * S->ntot);
     if (P->exc_kind == SFDO_EXC_BOW)
       for (int r = 0; r < S->ntot; ++r) x[r] -= k * k * force * S->zsol[r];
     band_mul(S, S->band0, x, tmp);
     double num = 0, den = 0;
     for (int r = 0; r < S->ntot; ++r) {
-      num = fmax(num, fabs(tmp[r] - S->rhs0[r]));
-      den = fmax(den, fabs(S->rhs0[r]));
+      num = fmax(num, NMAG(tmp[r] - S->rhs0[r]));
+      den = fmax(den, NMAG(S->rhs0[r]));
     }
     S->last_resid = den > 0 ? num / den : num;
   }
   /* excitation power delivered to the string, F I(delta_t. u) (Eqs. 5, 6) */
-  double unew_e = 0, uold_e = 0;
+  num_t unew_e = 0, uold_e = 0;
   for (int a = 0; a < 2; ++a) {
     const int la = S->e_node[a];
     if (P->exc_kind == SFDO_EXC_PLUCK || la <= 0 || la >= nt) continue;
@@ -669,8 +714,8 @@ static int step(sfdo_string* S) {
   }
   if (P->exc_kind == SFDO_EXC_HAMMER) {
     const double M = P->ham_mass / (P->rho_a * P->length);
-    const double eta_new = S->sol[S->hrow] - unew_e;
-    const double eta_old = S->uhp - uold_e;
+    const num_t eta_new = S->sol[S->hrow] - unew_e;
+    const num_t eta_old = S->uhp - uold_e;
     force = M * hamG * 0.5 * (eta_new + eta_old);
   }
   S->last_F = force;
@@ -682,13 +727,13 @@ static int step(sfdo_string* S) {
   if (P->exc_kind == SFDO_EXC_HAMMER) { S->uhp = S->uh; S->uh = S->sol[S->hrow]; }
   S->n += 1;
   for (int l = 0; l < S->nu; ++l)
-    if (!isfinite(S->u[l])) return -3;
+    if (!isfinite(RE(S->u[l]))) return -3;
   return 0;
 }
 
 /* Output sample y^j = L I(x_o) u^j, j = 0, 1, 2, ... (reading A10), or the
  * longitudinal displacement at the pickup (out_channel 1). */
-int sfdo_run(sfdo_string* S, int64_t n, double* y) {
+static int run_samples(sfdo_string* S, int64_t n, num_t* y) {
   if (!S || n < 0) return -1;
   for (int64_t s = 0; s < n; ++s) {
     const int64_t j = S->next_out;
@@ -697,16 +742,19 @@ int sfdo_run(sfdo_string* S, int64_t n, double* y) {
       if (rc) return rc;
     }
     if (S->p.out_channel == 1) {   /* longitudinal displacement at the pickup (Sec. 4.2) */
-      const double* zs = (j == S->n) ? S->z : S->zp;
+      const num_t* zs = (j == S->n) ? S->z : S->zp;
       y[s] = S->p.length * (S->ol_w[0] * Z(S, zs, S->ol_node[0]) + S->ol_w[1] * Z(S, zs, S->ol_node[1]));
     } else {
-      const double* src = (j == S->n) ? S->u : S->up;
+      const num_t* src = (j == S->n) ? S->u : S->up;
       y[s] = S->p.length * interp(S, src, S->o_node, S->o_w);
     }
     S->next_out++;
   }
   return 0;
 }
+
+#ifndef SFDO_COMPLEX
+int sfdo_run(sfdo_string* S, int64_t n, double* y) { return run_samples(S, n, y); }
 
 int64_t sfdo_time_level(const sfdo_string* S) { return S ? S->n : -1; }
 
@@ -755,3 +803,19 @@ int sfdo_run_batch(const sfdo_spec* specs, int32_t n_str, const int64_t* n_sampl
   }
   return err ? -err : used;
 }
+#else
+/* Complex-step derivative of the output with respect to one parameter
+ * (declared in sfd_oracle.h; built with -DSFDO_COMPLEX only). */
+int sfdo_cs_run(const sfdo_spec* s, int which, double h, int64_t n, double* y, double* dy) {
+  if (!s || which < 0 || which > 4 || !(h > 0) || n < 0 || !y || !dy) return -1;
+  sfdo_string* S = create_string(s, which, h);
+  if (!S) return -1;
+  num_t* yc = malloc(sizeof(num_t) * (size_t)(n > 0 ? n : 1));
+  int rc = yc ? run_samples(S, n, yc) : -5;
+  if (rc == 0)
+    for (int64_t j = 0; j < n; ++j) { y[j] = creal(yc[j]); dy[j] = cimag(yc[j]) / h; }
+  free(yc);
+  sfdo_destroy(S);
+  return rc;
+}
+#endif

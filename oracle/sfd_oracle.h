@@ -129,6 +129,17 @@ int sfdo_run_batch(const sfdo_spec* specs, int32_t n_str,
                    const int64_t* n_samples, const int64_t* offsets,
                    double* y, int32_t n_threads);
 
+/* Complex-step derivative (a second build of the same source with
+ * -DSFDO_COMPLEX, where the scalar is a complex double; this function exists
+ * only in that build).  Runs string s for n samples with parameter `which`
+ * (0 kappa, 1 alpha, 2 sigma0, 3 sigma1, 4 the pluck amplitude, hammer
+ * velocity or bow velocity) given the imaginary part h, and writes y (the
+ * output) and dy = dy/d(parameter) = Im(y)/h, exact to rounding wherever the
+ * path is smooth in the parameter (no hammer contact starting or ending, no
+ * stick/slip switch, within the perturbation).  Use n_t_override and
+ * n_l_override to hold the grid fixed.  0, or a negative code. */
+int sfdo_cs_run(const sfdo_spec* s, int which, double h, int64_t n, double* y, double* dy);
+
 #ifdef __cplusplus
 }
 #endif

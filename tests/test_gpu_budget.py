@@ -13,10 +13,11 @@ so the level n seen by H^{n+1/2} and by H^{n-1/2} differ by the rounding of
 u, eps |u| per node (eps = 2^-24); the energy terms linear in u^{n+1} move by
 about 2 eps H per step (H the largest energy), and the FP32 solve adds
 errors proportional to the small accelerations.  The bar per step is
-64 eps H; over the steps without force the summed change (the energy drift
-of the free string) must stay within 1e-5 H.  The hammer's force is the
-second difference of u_H, whose increments lose log2(|u_H| / |D u_H|) bits,
-so the contact law is held to 2^-13 of the largest force."""
+16 eps H (measured: at most 6 eps); over the steps without force the summed
+change (the energy drift of the free string) must stay within 1e-5 H
+(measured: 3e-7).  The hammer's force is the second difference of u_H,
+whose increments lose log2(|u_H| / |D u_H|) bits, so the contact law is
+held to 2^-14 of the largest force (measured: 1.6e-5 at most)."""
 
 import numpy as np
 import pytest
@@ -89,9 +90,9 @@ def test_hammer_power_budget(sfd, ctx, f0, kappa, alpha, vel, smem):
           f"({np.abs(r).max() / Hmax / EPS:.1f} eps), contact law {np.abs(c).max() / np.abs(F).max():.3e}, "
           f"contact steps {contact.sum()}, free drift {abs(r[~contact].sum()) / Hmax:.3e}")
     assert contact.sum() > 20 and (~contact).sum() > 1000
-    assert np.abs(r).max() <= 64 * EPS * Hmax
+    assert np.abs(r).max() <= 16 * EPS * Hmax
     assert abs(r[~contact].sum()) <= 1e-5 * Hmax
-    assert np.abs(c).max() <= 2.0 ** -13 * np.abs(F).max()
+    assert np.abs(c).max() <= 2.0 ** -14 * np.abs(F).max()
 
 
 @pytest.mark.parametrize("f0,kappa,alpha,env,smem", [(196.0, 1.0, 2.0, False, False),
@@ -109,6 +110,6 @@ def test_bow_power_budget(sfd, ctx, f0, kappa, alpha, env, smem):
           f"{np.abs(rs).max() / Hmax:.3e} ({np.abs(rs).max() / Hmax / EPS:.1f} eps), stick excess "
           f"{(stick.max() / Hmax / EPS) if n_stick else 0:.1f} eps")
     assert n_slip > 100
-    assert np.abs(rs).max() <= 64 * EPS * Hmax
+    assert np.abs(rs).max() <= 16 * EPS * Hmax
     if n_stick:
-        assert stick.max() <= 64 * EPS * Hmax
+        assert stick.max() <= 16 * EPS * Hmax
