@@ -2,10 +2,11 @@
 
 Bar (from the method's accuracy target): relative L2 error of the output
 waveform <= 1e-4 over the first 0.25 s, energy drift <= 1e-5 for the
-lossless scheme.  Bowed strings are compared over a short window at 1e-3,
-and over 0.5 s at 1e-3 wherever the FP64 trajectory is itself stable under
-FP32-sized state noise; a bowed note near a bifurcation, which that noise
-moves into another periodic regime, is compared by its level."""
+lossless scheme.  Bowed strings are compared at 1e-4 over 0.125 s (every
+bowed string of the 256-string batch), and over 0.5 s at 1e-3 wherever the
+FP64 trajectory is itself stable under FP32-sized state noise; a bowed note
+near a bifurcation, which that noise moves into another periodic regime, is
+compared by its level."""
 
 import math
 
@@ -281,14 +282,37 @@ def test_pool_exhaustion_is_enomem(sfd):
         sfd.sfd_ctx_destroy(c)
 
 
+def contact_episodes(d, n):
+    """Separate hammer contacts of the oracle's trajectory over n samples."""
+    s = oracle.OracleString(d)
+    s.run(2)
+    episodes, inside = 0, False
+    for _ in range(n - 2):
+        s.run(1)
+        c = s.state()[4][3] > 0          # the contact stiffness G of the last step
+        episodes += c and not inside
+        inside = c
+    return episodes
+
+
+BOW_WINDOW = 6000   # 0.125 s
+
+
 def test_full_batch_parity(sfd, ctx):
     """The 256-string, 2 s mixed batch in the benchmark's launch configuration:
     the first 0.25 s of every plucked or struck string against the oracle
-    within 1e-4, or, where FP32 storage of the state alone moves the oracle
-    further (strongly nonlinear strings struck hard), within three times that
-    floor; the first 150 samples of every bowed string; every output finite;
-    and the whole 2 s note within 1e-4 for every 10th of the strings that
-    meet it over 0.25 s."""
+    within 1e-4, and the first 0.125 s of every bowed string within 1e-4
+    (measured: at most 3.4e-5 over the 96 bowed strings; over 0.25 s five of
+    them cross a bifurcation, see test_bowed_notes_over_half_a_second); every
+    output finite; the whole 2 s note within 1e-4 for every 10th of the
+    plucked or struck strings.
+
+    The one exception, measured and physical: a struck string whose hammer
+    chatters (four or more separate contacts within the window, the string
+    swinging back into the slower hammer) has a trajectory that grows
+    FP32-sized perturbations ~10^5-fold, so running the FP64 oracle with its
+    state rounded to FP32 after every step already moves it past 1e-4; such
+    a string is held to three times that floor.  Two of the 160 are."""
     strings = W.batch_mixed(256, seconds=2.0, seed=2)
     hs = [sfd.string_from_dict(ctx, d) for d in strings]
     b = sfd.sfd_batch_create(ctx, hs)
@@ -303,19 +327,21 @@ def test_full_batch_parity(sfd, ctx):
     y = out.cpu().numpy()
     assert np.all(np.isfinite(y))
     assert np.all(st == 0)
-    lens = [150 if d["excitation"]["kind"] == "bow" else 12000 for d in strings]
+    lens = [BOW_WINDOW if d["excitation"]["kind"] == "bow" else 12000 for d in strings]
     refs, _ = oracle.run_batch(strings, n_samples=lens)
     from fp32_floor import fp32_state_floor
     beyond = []
     for i, (n, ref) in enumerate(zip(lens, refs)):
         e = rel_l2(y[offs[i]:offs[i] + n], ref)
-        if n == 150:
-            assert e <= 1e-3, (i, e)
-        elif e > TOL:
-            floor = fp32_state_floor(strings[i], n)
-            assert floor > TOL and e <= 3 * floor, (i, e, floor)
-            beyond.append(i)
-    assert len(beyond) <= 3, beyond   # 2 of the 160 plucked or struck strings
+        if e <= TOL:
+            continue
+        d = strings[i]
+        assert d["excitation"]["kind"] == "hammer", (i, e)
+        assert contact_episodes(d, n) >= 4, (i, e, "no chatter")
+        floor = fp32_state_floor(d, n)
+        assert floor > TOL and e <= 3 * floor, (i, e, floor)
+        beyond.append(i)
+    assert len(beyond) <= 2, beyond
     # the whole 2 s note, for every 10th of the others (phase errors grow
     # with time: measured 2e-6 - 1.3e-5 over 2 s)
     full = [i for i, d in enumerate(strings) if d["excitation"]["kind"] != "bow" and i not in beyond][::10]
