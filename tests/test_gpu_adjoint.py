@@ -149,12 +149,12 @@ def test_vector_jacobian_product_matches_the_oracle(sfd, ctx):
     the residual weights w = dJ/dy of the GPU run, its result must equal
     sum_j w_j dy_j/dp of the FP64 oracle, whose derivatives are exact
     (complex step, grid held fixed).  What remains is that the adjoint
-    differentiates the FP32 trajectory, not the FP64 one: each component is
-    held to 1e-7 of the string's largest term plus 100 times that string's
-    FP32 trajectory error (rel-L2 of y against the oracle) of it.  kappa
-    moves the partials' phase in proportion to time, so its derivative on
-    the FP32 trajectory departs most from the FP64 one (measured: 63 times
-    the trajectory error, a plucked string's dJ/dkappa off by 2.2e-4)."""
+    differentiates the FP32 trajectory, not the FP64 one, whose outputs
+    differ by rel-L2 ~1e-6 here.  kappa and alpha move the partials' phase in
+    proportion to time, so their derivatives on the FP32 trajectory depart
+    most from the FP64 ones: measured up to 2.7e-4 of the component for
+    plucked strings, the other components within 2e-5.  Each component is
+    held to 1e-3 of itself plus 1e-6 of the string's largest term."""
     base, target = workload(8, N_SHORT)
     tgt = targets_of(target, N_SHORT)
     tape = sfd.sfd_tape_create(ctx, base, N_SHORT, 1024)
@@ -175,8 +175,9 @@ def test_vector_jacobian_product_matches_the_oracle(sfd, ctx):
         th = np.array(params_of(d))
         scale = np.max(np.abs(ref * th))
         err = np.abs(g[i] - ref) * th
-        print(f"vjp {i} {d['excitation']['kind']}: trajectory {ey:.2e}, worst err/scale {np.max(err) / scale:.2e}")
-        assert np.all(err <= (1e-7 + 100 * ey) * scale), (i, g[i], ref, ey)
+        print(f"vjp {i} {d['excitation']['kind']}: trajectory {ey:.2e}, err/scale per component "
+              + " ".join(f"{x:.1e}" for x in err / scale) + " rel " + " ".join(f"{x:.1e}" for x in err / np.maximum(np.abs(ref * th), 1e-300)))
+        assert np.all(err <= 1e-3 * np.abs(ref * th) + 1e-6 * scale), (i, g[i], ref, ey)
 
 
 def test_vector_jacobian_product_longitudinal_output(sfd, ctx):
