@@ -173,19 +173,6 @@ __device__ __forceinline__ bool sweep_converged(float e, float e_prev, int sweep
   return false;
 }
 
-// Predicted convergence after the first sweep: with the contraction rho
-// (the ratio of successive sweeps' changes, measured on recent steps) the
-// second sweep would change the longitudinal field by about rho e; when that
-// is below a quarter of the tolerance the second sweep's longitudinal half
-// would only confirm convergence, and the step ends with the transverse solve
-// against the field of the first sweep (which is then within the tolerance of
-// the converged one, as the measured rule would have accepted).  Steps with n
-// a multiple of kRhoEvery, and every step until rho is known, run the full
-// sweeps and measure rho.
-__device__ __forceinline__ bool predict_converged(float e, float rho, bool measure) {
-  return !measure && rho > 0.f && rho * e <= 0.25f * kSweepTol;
-}
-
 __device__ __forceinline__ float warp_max_nonneg(float v) {
   // non-negative floats order like their bit patterns
   return __uint_as_float(__reduce_max_sync(SFD_FULL, __float_as_uint(v)));

@@ -304,7 +304,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   int64_t n = scp->n, jnext = scp->next_out;
   const int64_t n_first = n;
   float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w, scz = scp->scale_z, scx = scp->scale_x;
-  float rho = scp->rho;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
   int64_t sweeps_total = scp->sweeps_total;
@@ -631,8 +630,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
         // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
         int sweep = 0;
         float e_prev = 0.f, mag_all = 0.f, mgx_all = 0.f;
-        const bool measure = (n % kRhoEvery) == 0 || !(rho > 0.f);
-        bool half = false;   // last pass: the transverse solve only (predict_converged)
         for (;;) {
           float az[MU], AZe[MU + 2];
 #pragma unroll
@@ -658,7 +655,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
             tri_solve_r<MU, 1>(SB, IV, CPr, FFr, GGr, AC, AC, lane, rdu);
           }
           if (refine) refine_solve(BC, AC);
-          if (half) { ++sweep; break; }
           // nodal d_+[g d(.)] of the new accelerations for the longitudinal rows
           {
             float ACe[MU + 2], fc[MU], fx[MU];
@@ -758,12 +754,8 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           mgx_all = fmaxf(mgx_all, mgx);
           const float e = warp_max_nonneg(el);
           ++sweep;
-          if (sweep_converged(e, e_prev, sweep)) {
-            if (sweep >= 2 && e_prev > 0.f) rho = e / e_prev;
-            break;
-          }
+          if (sweep_converged(e, e_prev, sweep)) break;
           if (sweep >= sweep_cap) { status |= kStNoConv; break; }
-          if (sweep == 1 && predict_converged(e, rho, measure)) half = true;
           e_prev = e;
         }
         sweeps_total += sweep;
@@ -871,7 +863,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
     scp->bow_w = bow_w;
     scp->scale_z = scz;
     scp->scale_x = scx;
-    scp->rho = rho;
     scp->status = status;
     scp->max_sweeps = max_sweeps;
     scp->sweeps_total = sweeps_total;

@@ -67,7 +67,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   Scalars* scp = Dp->sc;
   int64_t n = scp->n, jnext = scp->next_out;
   const int64_t n_first = n;
-  float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w, rho = scp->rho;
+  float uh = scp->uh, duh = scp->duh, bow_w = scp->bow_w;
   int status = scp->status;
   int max_sweeps = scp->max_sweeps;
   int64_t sweeps_total = scp->sweeps_total;
@@ -311,8 +311,6 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         // ---- stage 3: block Gauss-Seidel on (a, az) [and the response] ----
         int sweep = 0;
         float e_prev = 0.f;
-        const bool measure = (n % kRhoEvery) == 0 || !(rho > 0.f);
-        bool half = false;   // last pass: the transverse solve only (predict_converged)
         for (;;) {
           if (sweep > 0) {
             for (int r = 0; r < m_u; ++r) {
@@ -341,7 +339,6 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
             tri_solve(SUB, INV, CP, FF, GG, XP, m_u, lane, rdu);
           }
           __syncwarp();
-          if (half) { ++sweep; break; }
           for (int r = 0; r < m_u; ++r) {
             const int i = ub + r;
             if (i < n_u) {
@@ -373,12 +370,8 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
           __syncwarp();
           ++sweep;
           const float e = fmaxf(chg > 0.f ? chg / mag : 0.f, chx > 0.f ? chx / mgx : 0.f);
-          if (sweep_converged(e, e_prev, sweep)) {
-            if (sweep >= 2 && e_prev > 0.f) rho = e / e_prev;
-            break;
-          }
+          if (sweep_converged(e, e_prev, sweep)) break;
           if (sweep >= sweep_cap) { status |= kStNoConv; break; }
-          if (sweep == 1 && predict_converged(e, rho, measure)) half = true;
           e_prev = e;
         }
         sweeps_total += sweep;
@@ -482,7 +475,6 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
     scp->uh = uh;
     scp->duh = duh;
     scp->bow_w = bow_w;
-    scp->rho = rho;
     scp->status = status;
     scp->max_sweeps = max_sweeps;
     scp->sweeps_total = sweeps_total;

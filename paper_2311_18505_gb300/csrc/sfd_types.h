@@ -11,7 +11,6 @@ constexpr int kWarp = 32;
 constexpr int kMaxSweeps = 24;       // default cap of the coupled block Gauss-Seidel solve
 constexpr int kMaxSweepCap = 64;     // largest cap a context may set
 constexpr float kSweepTol = 5e-7f;   // relative change that ends the solve
-constexpr int kRhoEvery = 32;        // steps n with n % kRhoEvery == 0 measure the contraction
 
 enum ExcKind : int32_t { kPluck = 0, kHammer = 1, kBow = 2 };
 enum StatusBits : int32_t { kStUnstable = 1, kStNoConv = 2 };
@@ -27,8 +26,7 @@ struct Scalars {
   float bow_w;            // last bow slip speed |v_rel| (Newton warm start)
   float scale_z;          // string-wide scale of the longitudinal increment (solver test)
   float scale_x;          // string-wide scale of the unit-force response (solver test)
-  float rho;              // contraction of the coupled solve measured at the last full step
-                          // (the ratio of successive sweeps' changes; 0: not yet measured)
+  float pad_;
 };
 
 // Per-string descriptor (device memory, read-only in the kernel).
