@@ -233,7 +233,10 @@ sfd_status sfd_tape_backward(sfd_tape* t, const float* dy_device, double* grad) 
     // (the next segment's replay and job table follow in stream order)
   }
   std::vector<double> g(static_cast<size_t>(t->n) * kGradSlots);
-  SFD_CUDA(cudaMemcpy(g.data(), t->d_grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+  // on the context stream, after the last sweep (a plain cudaMemcpy would not
+  // wait for a non-blocking context stream)
+  SFD_CUDA(cudaMemcpyAsync(g.data(), t->d_grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+  SFD_CUDA(cudaStreamSynchronize(c->stream));
   c->d2h_bytes += sizeof(double) * g.size();
   // chain rule from the step's coefficients to the physical parameters
   // (grid held fixed; the transverse line carries the scale rho)
