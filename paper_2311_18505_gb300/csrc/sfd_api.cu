@@ -1127,30 +1127,34 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
   if (!s) return fail(SFD_EINVAL, "string is NULL");
   if (s->started) return fail(SFD_ESTATE, "set modulation before synthesizing");
   const double peak = std::isfinite(depth) ? modulation_peak(kind, depth) : 1.0;
-  if (peak > s->p.f0_max_ratio * (1.0 + 1e-12)) {
-    // the grid is re-derived for the modulation's peak (coarser: a faster
-    // wave), in a new pool block (nothing has run on the old one)
-    if (s->batch_refs > 0)
-      return fail(SFD_EBUSY, "the grid must grow to this modulation's peak: set it before adding the string to a batch");
-    sfd_ctx* c = s->ctx;
-    const sfd_string saved = *s;
-    sfd_status rg = regrid_host(s, peak);
-    if (rg == SFD_OK &&
-        static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z, s->h.z_jacobi)) * sizeof(float) > c->smem_optin)
-      rg = fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", s->n_t, s->n_l);
-    char* nb = nullptr;
-    if (rg == SFD_OK && !(nb = c->pool.alloc(block_bytes(s->h))))
-      rg = fail(SFD_ENOMEM, "device pool exhausted (%zu of %zu bytes used)", c->pool.used(), c->pool.size());
-    if (rg) {
-      *s = saved;
-      return rg;
-    }
-    c->pool.dealloc(saved.block);
-    s->block = nb;
-    carve(s);
+  if (!(peak > s->p.f0_max_ratio * (1.0 + 1e-12))) {
+    sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
+    if (rc) return rc;
+    stage_initial(s);
+    return SFD_OK;
   }
-  sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
-  if (rc) return rc;
+  // The grid is re-derived for the modulation's peak (coarser: a faster wave)
+  // in a new pool block; the string keeps its old grid and block unless the
+  // modulation is accepted (nothing has run on the old block).
+  if (s->batch_refs > 0)
+    return fail(SFD_EBUSY, "the grid must change for this modulation's peak: set it before adding the string to a batch");
+  sfd_ctx* c = s->ctx;
+  const sfd_string saved = *s;
+  sfd_status rc = regrid_host(s, peak);
+  if (rc == SFD_OK &&
+      static_cast<size_t>(warp_smem_floats(s->h.m_u, s->h.m_z, s->h.z_jacobi)) * sizeof(float) > c->smem_optin)
+    rc = fail(SFD_EINVAL, "grid (N_t=%d, N_l=%d) exceeds one warp's shared memory", s->n_t, s->n_l);
+  if (rc == SFD_OK) rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
+  char* nb = nullptr;
+  if (rc == SFD_OK && !(nb = c->pool.alloc(block_bytes(s->h))))
+    rc = fail(SFD_ENOMEM, "device pool exhausted (%zu of %zu bytes used)", c->pool.used(), c->pool.size());
+  if (rc) {
+    *s = saved;
+    return rc;
+  }
+  c->pool.dealloc(saved.block);
+  s->block = nb;
+  carve(s);
   stage_initial(s);
   return SFD_OK;
 }

@@ -279,5 +279,17 @@ def test_modulation_grows_the_grid_before_the_first_synthesis(sfd):
         assert ei.value.code == sfd.SFD_EBUSY
         sfd.sfd_batch_destroy(b)
         sfd.sfd_string_destroy(s)
+        # a refused modulation leaves the string as it was: grid, block and samples
+        plain = dict(d, gamma_max_ratio=1.0, modulation={"kind": "none"})
+        s = sfd.string_from_dict(ctx, plain)
+        grid = sfd.sfd_string_info(s)[:2]
+        with pytest.raises(sfd.SfdError) as ei:
+            sfd.sfd_set_modulation(s, sfd.SFD_MOD_VIBRATO, float("nan"), 300.0, 0.0, 0.0)
+        assert ei.value.code == sfd.SFD_EINVAL
+        assert sfd.sfd_string_info(s)[:2] == grid
+        ref = sfd.string_from_dict(ctx, plain)
+        assert np.array_equal(sfd.sfd_synthesize(s, 3000), sfd.sfd_synthesize(ref, 3000))
+        sfd.sfd_string_destroy(ref)
+        sfd.sfd_string_destroy(s)
     finally:
         sfd.sfd_ctx_destroy(ctx)
