@@ -57,9 +57,18 @@ FLOP_EXCITATION = 30.0    # per string-step with a hammer or bow (scalar solve +
 FLOP_RESPONSE_U = 10.0    # per transverse row for the unit-force response (nonlinear, forced)
 
 
-def algorithmic_flops(strings, grids, select=None) -> float:
+# The minimal counts per update of the survey of the method (prefactored
+# solves, no delta form): linear 17, nonlinear 40-55 (47.5 taken), longitudinal
+# 20-30 (25 taken), 10 per forced string-step plus 9 per transverse row.
+MINIMAL_COUNTS = (17.0, 47.5, 25.0, 10.0, 9.0)
+
+
+def algorithmic_flops(strings, grids, select=None, counts=None) -> float:
     """Algorithmic FLOPs of one synthesis of `strings` (optionally only the
-    indices in `select`)."""
+    indices in `select`), with this build's counts or `counts` = (linear u,
+    nonlinear u, z, per forced step, per forced u row)."""
+    lin_u, nl_u, z_row, exc, resp = counts or (FLOP_U_LINEAR, FLOP_U_NONLINEAR, FLOP_Z, FLOP_EXCITATION,
+                                               FLOP_RESPONSE_U)
     tot = 0.0
     for idx, (d, (nt, nl)) in enumerate(zip(strings, grids)):
         if select is not None and idx not in select:
@@ -67,9 +76,9 @@ def algorithmic_flops(strings, grids, select=None) -> float:
         n_u = nt - 1
         linear = d["alpha"] == 1.0
         n_z = 0 if linear else max(nl - 1, 0)
-        per = n_u * (FLOP_U_LINEAR if linear else FLOP_U_NONLINEAR) + n_z * FLOP_Z
+        per = n_u * (lin_u if linear else nl_u) + n_z * z_row
         if d["excitation"]["kind"] != "pluck":
-            per += FLOP_EXCITATION + (0.0 if linear else n_u * FLOP_RESPONSE_U)
+            per += exc + (0.0 if linear else n_u * resp)
         tot += per * (d["n_samples"] - 2)
     return tot
 
@@ -489,6 +498,7 @@ def run_ours(args, ws, rank, local):
         dom_idx = set(range(len(strings)))
         kernel = "synth_kernel_* (all classes, concurrent in one graph replay)"
     achieved = algorithmic_flops(strings, grids, dom_idx) / (dom_ms / 1e3) / 1e12
+    achieved_min = algorithmic_flops(strings, grids, dom_idx, MINIMAL_COUNTS) / (dom_ms / 1e3) / 1e12
     # DRAM traffic and ncu pipe / shared-memory fractions from the committed
     # summaries of this workload's kernels (None if taken on other sources)
     tr = profile_figures(f"synth_kernel_dram_{args.workload}.md") if ws == 1 else None
@@ -527,6 +537,7 @@ def run_ours(args, ws, rank, local):
                              "one persistent kernel per class per step, one warp per string"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "fp32_frac": achieved / peak,
+                     "frac_minimal_counts": achieved_min / peak,
                      "smem_frac": (float(sm_prof["smem_pct_of_peak"]) / 100.0
                                    if sm_prof and "smem_pct_of_peak" in sm_prof else None),
                      "fma_pipe_frac": (float(sm_prof["fma_pipe_pct_of_peak"]) / 100.0
