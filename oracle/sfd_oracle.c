@@ -188,14 +188,18 @@ static void bow_controls(const sfdo_spec* P, double t, double* v, double* f, dou
 }
 
 /* f0 modulation (abstract; Sec. 1 lists f0 modulation among the
- * stochastic parameters).  gamma^n for the step n -> n+1. */
+ * stochastic parameters).  gamma^n for the step n -> n+1, t = n k: vibrato
+ * gamma 2^{(c/1200) sin(2 pi f_v t + phi)}; glissando gamma 2^{D min(t, T) / T},
+ * a glide over T that then holds at 2^D (the peak the grid is sized for). */
 static double gamma_at(const sfdo_string* S, int64_t n) {
   const double t = (double)n * S->k;
   const sfdo_spec* p = &S->p;
   if (p->mod_kind == SFDO_MOD_VIBRATO)
     return p->gamma * pow(2.0, (p->mod_depth / 1200.0) * sin(2.0 * PI_D * p->mod_rate * t + p->mod_phase));
-  if (p->mod_kind == SFDO_MOD_GLISS && p->mod_duration > 0)
-    return p->gamma * pow(2.0, p->mod_depth * t / p->mod_duration);
+  if (p->mod_kind == SFDO_MOD_GLISS && p->mod_duration > 0) {
+    const double tg = t < p->mod_duration ? t : p->mod_duration;
+    return p->gamma * pow(2.0, p->mod_depth * tg / p->mod_duration);
+  }
   return p->gamma;
 }
 

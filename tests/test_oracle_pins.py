@@ -128,19 +128,20 @@ def test_dst_modal_solution(sigma0, sigma1, kappa):
 
 def _wave_speeds(d, n):
     """gamma^n of the step n -> n+1 (reading A14): vibrato
-    gamma 2^{(c/1200) sin(2 pi f_v n k + phi)}, glissando gamma 2^{D n k / T}."""
+    gamma 2^{(c/1200) sin(2 pi f_v n k + phi)}, glissando gamma 2^{D min(n k, T) / T}."""
     g, t = 2.0 * d["f0"], np.arange(n) / d["fs"]
     m = d["modulation"]
     if m["kind"] == "vibrato":
         return g * 2.0 ** (m["depth"] / 1200.0 * np.sin(2 * math.pi * m["rate"] * t + m["phase"]))
     if m["kind"] == "gliss":
-        return g * 2.0 ** (m["depth"] * t / m["duration"])
+        return g * 2.0 ** (m["depth"] * np.minimum(t, m["duration"]) / m["duration"])
     return np.full(n, g)
 
 
 @pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 6.0, "depth": 40.0, "phase": 0.7},
                                  {"kind": "gliss", "depth": 1.0, "duration": 0.25},
-                                 {"kind": "gliss", "depth": -0.5, "duration": 0.25}])
+                                 {"kind": "gliss", "depth": -0.5, "duration": 0.25},
+                                 {"kind": "gliss", "depth": 0.7, "duration": 0.1}])
 def test_modulated_modal_recursion(mod):
     """A linear simply-supported string with a modulated wave speed: each sine
     mode's recurrence, stepped with the step's gamma^n, gives the oracle's
@@ -155,7 +156,8 @@ def test_modulated_modal_recursion(mod):
 
 
 @pytest.mark.parametrize("mod", [{"kind": "vibrato", "rate": 150.0, "depth": 300.0, "phase": 0.4},
-                                 {"kind": "gliss", "depth": 1.0, "duration": 0.00625}])
+                                 {"kind": "gliss", "depth": 1.0, "duration": 0.00625},
+                                 {"kind": "gliss", "depth": 0.6, "duration": 0.003}])
 @pytest.mark.parametrize("alpha,exi", [(3.0, 0), (6.0, 1), (2.0, 2)])
 def test_modulated_brute_force(mod, alpha, exi):
     """Nonlinear strings (plucked, struck, bowed) with a fast vibrato or
@@ -222,6 +224,26 @@ def test_glissando_pitch_rises_an_octave():
     f_a = peak_frequency(y[:9600], d["fs"], 80.0, 160.0)
     f_b = peak_frequency(y[38400:], d["fs"], 160.0, 280.0)
     assert f_b / f_a == pytest.approx(2.0 ** 0.8, rel=5e-3)
+
+
+def test_glissando_holds_at_its_end():
+    """After its duration T an octave glissando holds at 2^D: from then on the
+    string steps with gamma 2^1 = 2 gamma on the grid sized for that peak,
+    which is the unmodulated string an octave up (same grid, same
+    coefficients), so the fundamental measured after T is that string's
+    (within 0.2 %), and the held note stays bounded for 12 T (a glide that
+    kept rising would reach 2^12 and leave the grid's stability bound)."""
+    d = W.make(kappa=0.1, sigma0=0.2, sigma1=1e-6, modulation={"kind": "gliss", "depth": 1.0, "duration": 0.1},
+               excitation={"kind": "pluck", "amp": 1e-3, "pos": 0.3}, n_samples=57600)
+    up = W.make(kappa=0.1, sigma0=0.2, sigma1=1e-6, f0=2.0 * d["f0"],
+                excitation={"kind": "pluck", "amp": 1e-3, "pos": 0.3}, n_samples=57600)
+    assert oracle.grid(d) == oracle.grid(up)
+    y, y_up = oracle.run(d), oracle.run(up)
+    assert np.all(np.isfinite(y))
+    f_held = peak_frequency(y[9600:], d["fs"], 160.0, 280.0)
+    f_up = peak_frequency(y_up[9600:], d["fs"], 160.0, 280.0)
+    assert f_held == pytest.approx(f_up, rel=2e-3)
+    assert np.max(np.abs(y[28800:])) <= np.max(np.abs(y[:28800]))
 
 
 def test_zero_depth_modulation_is_none():
