@@ -165,7 +165,9 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
 
 /* f0 modulation (Sec. 1): kind SFD_MOD_VIBRATO, gamma^n = gamma 2^{(c/1200)
  * sin(2 pi rate t + phase)} with depth c in cents; SFD_MOD_GLISS, gamma^n =
- * gamma 2^{D t / duration} with depth D in octaves.  The grid must be stable
+ * gamma 2^{D min(t, duration) / duration} with depth D in octaves (a glide
+ * that holds at 2^D once t reaches the duration).  t = n k for the step from
+ * level n.  SFD_MOD_NONE removes a modulation.  The grid must be stable
  * at the modulation's peak wave speed (sfd_modulation_peak): when the string
  * was created with a smaller f0_max_ratio, its grid is derived again for the
  * peak (a faster wave needs a coarser grid, so N_t and N_l shrink; the

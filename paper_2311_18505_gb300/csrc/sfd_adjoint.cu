@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const float lam2_0f = Dp->lam2, lam2lo_0f = Dp->lam2_lo, lam2l_0f = Dp->lam2l;
   const float ca_0f = Dp->ca, cb_0f = Dp->cb, cz_0f = Dp->cz;
   const int mod_kind = Dp->mod_kind;
-  const double mod_inc = Dp->mod_inc, mod_phase0 = Dp->mod_phase0;
   const float mod_depth2 = Dp->mod_depth2;
   R lam2 = static_cast<R>(lam2_0f) + static_cast<R>(lam2lo_0f), lam2l = lam2l_0f;
   R ca = ca_0f, cb = cb_0f, cz = cz_0f, rmd = 1.0;
@@ -325,14 +324,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   for (int64_t m = J.m_end; m > J.m_start; --m) {
     const int64_t n = m - 1;
     if (mod_kind != 0) {   // the step n -> n + 1 as the forward took it
-      float rm = 1.f;
-      if (mod_kind == 1) {
-        double t = fma(static_cast<double>(n), mod_inc, mod_phase0);
-        t -= floor(t);
-        rm = exp2f(mod_depth2 * sinf(6.28318530717958647f * static_cast<float>(t)));
-      } else if (mod_kind == 2) {
-        rm = exp2f(static_cast<float>(mod_inc * static_cast<double>(n)));
-      }
+      const float rm = mod_factor(mod_kind, Dp->mod_inc_fx, Dp->mod_phase_fx, mod_depth2, Dp->mod_inc, Dp->mod_hold,
+                                  Dp->mod_n_end, n);
       const float l2 = lam2_0f * rm;
       lam2 = static_cast<R>(l2) + static_cast<R>(fmaf(lam2_0f, rm, -l2) + lam2lo_0f * rm);
       lam2l = static_cast<R>(lam2l_0f * rm);

@@ -596,28 +596,56 @@ sfd_status regrid_host(sfd_string* s, double ratio) {
   return SFD_OK;
 }
 
-// f0 modulation on the host copy of the descriptor (reading A14).
+// Fractional part of x as a 64-bit fixed-point fraction (x 2^64 mod 2^64).
+uint64_t frac_fx(double x) {
+  const double f = x - std::floor(x);             // [0, 1]: 1 only by rounding, taken as 0
+  const double p = std::ldexp(f, 64);
+  return p >= 18446744073709551616.0 ? 0 : static_cast<uint64_t>(p);
+}
+
+// f0 modulation on the host copy of the descriptor (reading A14).  Every
+// modulation field is rewritten, so the descriptor depends only on the last
+// modulation set.
 sfd_status apply_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth, double phase_rad,
                             double duration_s) {
   Desc& D = s->h;
-  if (kind == SFD_MOD_NONE) {
-    D.mod_kind = 0;
-  } else if (kind == SFD_MOD_VIBRATO) {
-    if (!std::isfinite(rate_hz) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad vibrato");
+  if (kind == SFD_MOD_VIBRATO) {
+    if (!std::isfinite(rate_hz) || !std::isfinite(depth) || !std::isfinite(phase_rad))
+      return fail(SFD_EINVAL, "bad vibrato");
     if (std::pow(2.0, std::fabs(depth) / 1200.0) > s->p.f0_max_ratio * (1.0 + 1e-12))
       return fail(SFD_EINVAL, "vibrato peak exceeds the grid's f0_max_ratio");
-    D.mod_kind = 1;
-    D.mod_inc = rate_hz * s->k;
-    D.mod_phase0 = phase_rad / (2.0 * kPi);
-    D.mod_depth2 = static_cast<float>(2.0 * depth / 1200.0);
   } else if (kind == SFD_MOD_GLISS) {
-    if (!(duration_s > 0) || !std::isfinite(depth)) return fail(SFD_EINVAL, "bad glissando");
+    if (!(duration_s > 0) || !std::isfinite(duration_s) || !std::isfinite(depth))
+      return fail(SFD_EINVAL, "bad glissando");
     if (std::pow(2.0, std::max(0.0, depth)) > s->p.f0_max_ratio * (1.0 + 1e-12))
       return fail(SFD_EINVAL, "glissando peak exceeds the grid's f0_max_ratio");
-    D.mod_kind = 2;
-    D.mod_inc = 2.0 * depth * s->k / duration_s;
-  } else {
+  } else if (kind != SFD_MOD_NONE) {
     return fail(SFD_EINVAL, "bad modulation kind");
+  }
+  D.mod_kind = 0;
+  D.mod_inc_fx = 0;
+  D.mod_phase_fx = 0;
+  D.mod_depth2 = 0.f;
+  D.mod_inc = 0.f;
+  D.mod_hold = 0.f;
+  D.mod_n_end = 0;
+  if (kind == SFD_MOD_VIBRATO) {
+    D.mod_kind = 1;
+    D.mod_inc_fx = frac_fx(rate_hz * s->k);
+    D.mod_phase_fx = frac_fx(phase_rad / (2.0 * kPi));
+    D.mod_depth2 = static_cast<float>(2.0 * depth / 1200.0);
+  } else if (kind == SFD_MOD_GLISS) {
+    D.mod_kind = 2;
+    D.mod_inc = static_cast<float>(2.0 * depth * s->k / duration_s);
+    D.mod_hold = static_cast<float>(2.0 * depth);
+    // first step n with n k >= T (the same comparison as a bow release)
+    const double nt = std::ceil(duration_s * s->p.fs);
+    int64_t n = nt < 9.0e18 ? static_cast<int64_t>(nt) : INT64_MAX;
+    if (n != INT64_MAX) {
+      while (n > 0 && static_cast<double>(n - 1) * s->k >= duration_s) --n;
+      while (static_cast<double>(n) * s->k < duration_s) ++n;
+    }
+    D.mod_n_end = n;
   }
   return SFD_OK;
 }

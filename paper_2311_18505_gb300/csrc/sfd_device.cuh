@@ -144,7 +144,8 @@ __device__ __forceinline__ void tri_solve(const T* __restrict__ SUB, const T* __
   if (lane == kWarp - 1) e0n = 0;
   T D = dlast - rd.cl * e0n;
 #pragma unroll
-  for (int l = 0; l < 5; ++l) {   // skipped levels carry zero multipliers
+  for (int l = 0; l < 5; ++l) {
+    if (l >= rd.nlev) break;      // the factorisation dropped the remaining levels (warp-uniform)
     const int s = 1 << l;
     T Dm = __shfl_up_sync(SFD_FULL, D, s);
     T Dp = __shfl_down_sync(SFD_FULL, D, s);
@@ -191,6 +192,24 @@ __device__ __forceinline__ float zinterp(const float* __restrict__ A, int node, 
   const float a = (node >= 1 && node - 1 < n_z) ? A[node - 1] : 0.f;
   const float b = (node >= 0 && node < n_z) ? A[node] : 0.f;
   return (1.f - w) * a + w * b;
+}
+
+// Wave-speed factor rm = (gamma^n / gamma)^2 of the step from level n
+// (reading A14), which scales every gamma^2 term.  Vibrato: 2^{(2c/1200)
+// sin(2 pi t)} with the phase t = frac(n f_v k + phi / 2 pi) kept as a 64-bit
+// fixed-point fraction, where the integer product's wrap-around is the
+// fractional part (exact for any n, and no FP64 arithmetic, which runs at a
+// small fraction of the FP32 rate on this GPU, enters the step); glissando:
+// 2^{2 D min(n k, T) / T}, i.e. held at 2^{2D} from step n_end on.
+__device__ __forceinline__ float mod_factor(int kind, uint64_t inc_fx, uint64_t phase_fx, float depth2,
+                                            float inc, float hold, int64_t n_end, int64_t n) {
+  if (kind == 1) {
+    const uint64_t t_fx = static_cast<uint64_t>(n) * inc_fx + phase_fx;
+    const float t = static_cast<float>(static_cast<uint32_t>(t_fx >> 40)) * 5.9604644775390625e-8f;   // 2^-24
+    return exp2f(depth2 * sinf(6.28318530717958647f * t));
+  }
+  if (kind == 2) return exp2f(n < n_end ? inc * static_cast<float>(n) : hold);
+  return 1.f;
 }
 
 // Bow controls of step n from the descriptor's breakpoint envelopes

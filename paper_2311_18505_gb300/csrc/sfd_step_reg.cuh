@@ -160,7 +160,8 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
   if (lane == kWarp - 1) { e1 = 0.f; e2 = 0.f; }
   float D1 = dl1 - rd.cl * e1, D2 = dl2 - rd.cl * e2;
 #pragma unroll
-  for (int l = 0; l < 5; ++l) {   // skipped levels carry zero multipliers
+  for (int l = 0; l < 5; ++l) {
+    if (l >= rd.nlev) break;      // the factorisation dropped the remaining levels (warp-uniform)
     const int s = 1 << l;
     float m1 = __shfl_up_sync(SFD_FULL, D1, s), q1 = __shfl_down_sync(SFD_FULL, D1, s);
     float m2 = 0.f, q2 = 0.f;
@@ -258,8 +259,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   const float ca_0 = Dp->ca, cb_0 = Dp->cb, cz_0 = Dp->cz;
   const float bsgn = Dp->boundary == 1 ? -1.f : 1.f;
   const int mod_kind = Dp->mod_kind;
-  const double mod_inc = Dp->mod_inc, mod_phase0 = Dp->mod_phase0;
-  const float mod_depth2 = Dp->mod_depth2;
+  const uint64_t mod_inc_fx = Dp->mod_inc_fx, mod_phase_fx = Dp->mod_phase_fx;
+  const int64_t mod_n_end = Dp->mod_n_end;
+  const float mod_depth2 = Dp->mod_depth2, mod_inc = Dp->mod_inc, mod_hold = Dp->mod_hold;
   const float ham_k2w = Dp->ham_k2w, ham_expo = Dp->ham_expo, ham_M = Dp->ham_M;
   const float bow_F = Dp->bow_F, bow_v = Dp->bow_v, bow_a = Dp->bow_a, bow_eps = Dp->bow_eps;
   const float kk = Dp->k, k2 = Dp->k2;
@@ -324,11 +326,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   }
   __syncwarp();
   if (paired) group_sync(bar_id, ng);   // both halves of the longitudinal state are loaded
-  auto interp_z = [&](const float* A, int i) {
-    const int mm = TMIs[i];
-    const float w = TMWs[i];
-    return (1.f - w) * A[mm - 1] + w * A[mm];
-  };
   // (P^T F) at longitudinal node m = sum over the transverse nodes l of
   // P[l, m] F_l, P the linear interpolation from the longitudinal to the
   // transverse nodes.  Transverse node l (row l - 1) lies in the longitudinal
@@ -369,6 +366,13 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
       scan_lv = l + 1;
     }
   }
+  // A longitudinal field interpolated to the lane's transverse row r (the
+  // row's transfer map is held in registers; pad rows read the zero cell).
+  auto interp_zr = [&](const float* A, int r) {
+    const int mm = mmr[r];
+    const float w = wr[r];
+    return (1.f - w) * A[mm - 1] + w * A[mm];
+  };
   // Interval sums of (1 - w) f and w f for NF fields at once (independent
   // chains interleaved), stored into their slot pairs.
   auto emit2 = [&](const float (&f)[MU], float* S0, float* S1, const float (&g)[MU], float* T0, float* T1,
@@ -515,14 +519,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   while (jnext < j_end) {
     if (jnext > n && !(status & kStUnstable)) {
       // ======================= one step n -> n+1 =======================
-      float rm = 1.f;
-      if (mod_kind == 1) {
-        double t = fma(static_cast<double>(n), mod_inc, mod_phase0);
-        t -= floor(t);
-        rm = exp2f(mod_depth2 * sinf(6.28318530717958647f * static_cast<float>(t)));
-      } else if (mod_kind == 2) {
-        rm = exp2f(static_cast<float>(mod_inc * static_cast<double>(n)));
-      }
+      const float rm = mod_factor(mod_kind, mod_inc_fx, mod_phase_fx, mod_depth2, mod_inc, mod_hold, mod_n_end, n);
       const float lam2 = lam2_0 * rm, lam2l = lam2l_0 * rm;
       // low part of lam2_0 * rm (exact product residual plus the stored low part)
       const float lam2_lo = fmaf(lam2_0, rm, -lam2) + lam2lo_0 * rm;
@@ -562,7 +559,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
       if (has_z) {
         float zt[MU];
 #pragma unroll
-        for (int r = 0; r < MU; ++r) zt[r] = interp_z(Z, ub + r);
+        for (int r = 0; r < MU; ++r) zt[r] = interp_zr(Z, r);
         extend1<MU>(zt, ZTe, lane);
       }
       float RA[MU], fv[MU];
@@ -633,7 +630,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
         for (;;) {
           float az[MU], AZe[MU + 2];
 #pragma unroll
-          for (int r = 0; r < MU; ++r) az[r] = interp_z(AZ, ub + r);
+          for (int r = 0; r < MU; ++r) az[r] = interp_zr(AZ, r);
           extend1<MU>(az, AZe, lane);
 #pragma unroll
           for (int r = 0; r < MU; ++r)
@@ -644,7 +641,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           if (need_resp) {
             float xz[MU], XZe[MU + 2];
 #pragma unroll
-            for (int r = 0; r < MU; ++r) xz[r] = interp_z(XZ, ub + r);
+            for (int r = 0; r < MU; ++r) xz[r] = interp_zr(XZ, r);
             extend1<MU>(xz, XZe, lane);
             load_J(XP);
 #pragma unroll

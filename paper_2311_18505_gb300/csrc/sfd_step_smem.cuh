@@ -205,14 +205,8 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
   while (jnext < j_end) {
     if (jnext > n && !(status & kStUnstable)) {
       // ======================= one step n -> n+1 =======================
-      float rm = 1.f;
-      if (mod_kind == 1) {
-        double t = fma(static_cast<double>(n), Dp->mod_inc, Dp->mod_phase0);
-        t -= floor(t);
-        rm = exp2f(Dp->mod_depth2 * sinf(6.28318530717958647f * static_cast<float>(t)));
-      } else if (mod_kind == 2) {
-        rm = exp2f(static_cast<float>(Dp->mod_inc * static_cast<double>(n)));
-      }
+      const float rm = mod_factor(mod_kind, Dp->mod_inc_fx, Dp->mod_phase_fx, Dp->mod_depth2, Dp->mod_inc,
+                                  Dp->mod_hold, Dp->mod_n_end, n);
       const float lam2 = lam2_0 * rm, lam2l = lam2l_0 * rm;
       // low part of lam2_0 * rm (exact product residual plus the stored low part)
       const float lam2_lo = fmaf(lam2_0, rm, -lam2) + lam2lo_0 * rm;

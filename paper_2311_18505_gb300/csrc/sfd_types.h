@@ -69,10 +69,13 @@ struct Desc {
   float k;                // time step
   float k2;               // k^2
   int64_t bow_release_n;  // first step index with F_B = 0 (INT64_MAX: never)
-  // modulation: factor (gamma^n / gamma)^2 per step
-  double mod_inc;         // vibrato: rate k (cycles per step); gliss: 2 D k / T
-  double mod_phase0;      // vibrato: phase / (2 pi)
+  // modulation: factor (gamma^n / gamma)^2 per step (mod_factor)
+  uint64_t mod_inc_fx;    // vibrato: f_v k cycles per step, as a 64-bit fixed-point fraction
+  uint64_t mod_phase_fx;  // vibrato: phase / (2 pi), the same
+  int64_t mod_n_end;      // glissando: first step n with n k >= T (held from there on)
   float mod_depth2;       // vibrato: 2 c / 1200
+  float mod_inc;          // glissando: 2 D k / T per step
+  float mod_hold;         // glissando: 2 D
   float lam2_lo;          // lam2 + lam2_lo: wave coefficient to ~1e-15 (see fill_desc)
   // time-varying bow controls (Sec. 3.3.1): bow_env_n breakpoints (0: the
   // constant bow_v, bow_F, e_node / e_w), at steps bow_env_t (t fs) with

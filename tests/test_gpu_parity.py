@@ -209,7 +209,13 @@ def test_modulation(sfd, ctx):
                  n_samples=12000)
     gl = W.make(alpha=2.0, f0=90.0, modulation={"kind": "gliss", "depth": 1.0, "duration": 0.25},
                 n_samples=12000)
-    for d in (vib, gl):
+    # glides that end within the run and hold at 2^D (up and down)
+    held_up = W.make(alpha=2.0, f0=90.0, modulation={"kind": "gliss", "depth": 1.0, "duration": 0.08},
+                     n_samples=12000)
+    held_down = W.make(alpha=3.0, f0=150.0, modulation={"kind": "gliss", "depth": -0.6, "duration": 0.05},
+                       excitation={"kind": "hammer", "mass": 0.01, "vel": 1.0, "pos": 0.2, "omega": 3e3,
+                                   "alpha": 2.3}, n_samples=12000)
+    for d in (vib, gl, held_up, held_down):
         assert rel_l2(gpu_run(sfd, ctx, d), oracle.run(d)) <= TOL
 
 
