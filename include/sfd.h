@@ -209,6 +209,33 @@ sfd_status sfd_string_stats(const sfd_string* s, int32_t* status, int32_t* max_s
 
 sfd_status sfd_string_destroy(sfd_string* s);
 
+/* Checkpoint of a string: its full state (Sec. 3.4's two time levels w^{n-1},
+ * w^n as u, D, z, Dz; the hammer u_H^{n-1}, u_H^n of Eq. 6; the bow's slip
+ * speed kept as the friction root's warm start; the coupled solve's warm
+ * starts; the time level n, which also fixes the modulation phase and the
+ * bow envelope's position; status and solver statistics) together with its
+ * parameters and the excitation, bow envelope and modulation calls as last
+ * made, so that a note can be moved to another context, device or process
+ * and continue there.  Host memory, owned by the caller.  With buf NULL,
+ * *bytes receives the size needed; otherwise *bytes is buf's capacity on
+ * entry (SFD_EINVAL and the size needed in *bytes when it is too small) and
+ * the size written on return.  Pending work on the string's stream is
+ * waited for.  The format is this library's own, for the same library
+ * version and host byte order. */
+sfd_status sfd_string_save(const sfd_string* s, void* buf, size_t* bytes);
+
+/* A new string in ctx from a checkpoint of sfd_string_save: sfd_string_load
+ * then sfd_synthesize(n) gives exactly the samples that the saved string's
+ * next sfd_synthesize(n) would have given (bit for bit, on any device of
+ * this kind).  The saved set-up calls are made again through the public
+ * entry points, which check them, and the descriptor they give must equal
+ * the saved one byte for byte.  SFD_EINVAL for a buffer that is not a
+ * checkpoint of this format, is truncated, carries an inconsistent time
+ * level, or whose set-up does not give the saved descriptor (another build
+ * or host); SFD_ENOMEM when the pool has no room.  The checkpoint buffer is
+ * only read. */
+sfd_status sfd_string_load(sfd_ctx* ctx, const void* buf, size_t bytes, sfd_string** out);
+
 /* Batched form: n strings advanced together by one launch of the persistent
  * step kernel.  Strings stay owned by the caller's handles; a string in a
  * live batch cannot be destroyed (SFD_EBUSY). */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -170,6 +171,17 @@ struct sfd_string {
   double hammer_uh1 = 0;    // u_H^1 = v_H k (normalised), u_H^0 = 0
   double bow_pos = 0.5;     // x_B of sfd_excite_bow (constant position of an envelope)
   double exc_pos = 0.5;     // hammer or bow position (excitation node after a regrid)
+  // The set-up calls as last made, which a checkpoint replays (sfd_string_load):
+  // the excitation (pluck: amp, pos; hammer: mass, vel, pos, omega, alpha;
+  // bow: vel, force, pos, a, eps, release), the bow envelope (t, vel, force,
+  // pos; bit c of rec_env_mask: control c + 1 given) and the modulation
+  // (rate, depth, phase, duration).
+  int32_t rec_exc = kPluck;
+  double rec_exc_args[6] = {0.0, 0.5, 0.0, 0.0, 0.0, 0.0};
+  int32_t rec_env_n = 0, rec_env_mask = 0;
+  double rec_env[4][16] = {};
+  int32_t rec_mod = SFD_MOD_NONE;
+  double rec_mod_args[4] = {};
 };
 
 struct sfd_batch {
@@ -517,6 +529,43 @@ sfd_status init_host_string(const sfd_string_params& p, sfd_string* s) {
   return SFD_OK;
 }
 
+// Excitation fields of the descriptor at their values for a string that has
+// none (every excitation call starts from here, so the descriptor depends
+// only on the last excitation set, not on the ones before it).
+void clear_excitation(Desc& D) {
+  D.e_node = 0;
+  D.e_w = 0.f;
+  D.ham_M = D.ham_k2w = D.ham_expo = 0.f;
+  D.bow_F = D.bow_v = D.bow_a = D.bow_eps = 0.f;
+  D.bow_release_n = INT64_MAX;
+  D.bow_env_n = 0;
+  for (int j = 0; j < 16; ++j) {
+    D.bow_env_t[j] = 0.0;
+    D.bow_env_v[j] = D.bow_env_f[j] = D.bow_env_x[j] = 0.f;
+  }
+}
+
+// Record of the last excitation call (a new excitation drops the envelope,
+// as sfd_excite_bow does).
+void record_excitation(sfd_string* s, int32_t kind, std::initializer_list<double> args) {
+  s->rec_exc = kind;
+  int j = 0;
+  for (double a : args) s->rec_exc_args[j++] = a;
+  s->rec_env_n = 0;
+  s->rec_env_mask = 0;
+  for (auto& row : s->rec_env)
+    for (double& v : row) v = 0.0;
+}
+
+void record_modulation(sfd_string* s, int32_t kind, double rate_hz, double depth, double phase_rad,
+                       double duration_s) {
+  s->rec_mod = kind;
+  s->rec_mod_args[0] = rate_hz;
+  s->rec_mod_args[1] = depth;
+  s->rec_mod_args[2] = phase_rad;
+  s->rec_mod_args[3] = duration_s;
+}
+
 // Excitation of Sec. 3.3 / Eqs. 5-6 set on the host copy (as the
 // sfd_excite_* calls do; the pluck is the initial condition).
 sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
@@ -529,12 +578,14 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
     s->pluck_amp = ex.amp_m;
     s->pluck_pos = pos;
     fill_desc(s);
+    clear_excitation(s->h);
   } else if (ex.kind == kHammer) {
     if (!(ex.mass_kg > 0) || !(ex.omega_h > 0) || !(ex.alpha_h >= 1) || !std::isfinite(ex.vel_mps))
       return fail(SFD_EINVAL, "bad hammer parameters");
     s->exc = kHammer;
     s->pluck_amp = 0;
     fill_desc(s);
+    clear_excitation(s->h);
     point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
     s->exc_pos = pos;
     s->h.ham_M = static_cast<float>(ex.mass_kg / (q.linear_density * q.length_m));
@@ -547,6 +598,7 @@ sfd_status apply_excitation(sfd_string* s, const sfd_excitation& ex) {
     s->exc = kBow;
     s->pluck_amp = 0;
     fill_desc(s);
+    clear_excitation(s->h);
     point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
     s->exc_pos = pos;
     s->h.bow_F = static_cast<float>(ex.force_n / (q.linear_density * q.length_m * q.length_m));
@@ -843,6 +895,50 @@ sfd_status status_code(const Scalars& sc) {
   return SFD_OK;
 }
 
+// ---- checkpoints (sfd_string_save / sfd_string_load) ----
+// A checkpoint is [header | set-up record | descriptor | state]: the
+// parameters and the set-up calls as last made, the descriptor the library
+// derived from them (device pointers zeroed), and the string's device block
+// from its scalars on (Scalars, u, D, z, Dz and the two longitudinal warm
+// starts, in the block's own layout).  Loading replays the set-up calls
+// through the public entry points, which validate them, and accepts the
+// checkpoint only if the descriptor they give equals the saved one byte for
+// byte; so the kernels only ever see a descriptor this library computed,
+// and the resumed note continues bit for bit.
+constexpr char kCkptMagic[8] = {'S', 'F', 'D', 'S', 'T', 'R', 'C', 'K'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  uint64_t total_bytes;
+  uint32_t params_bytes, desc_bytes, scalars_bytes, record_bytes;
+  uint64_t state_offset, state_bytes;   // the state's place in the device block and its size
+  int32_t n_t, n_l, started, pad_;
+};
+
+struct CkptRecord {
+  sfd_string_params p;
+  int32_t exc, env_n, env_mask, mod;
+  double exc_args[6];
+  double env[4][16];
+  double mod_args[4];
+};
+
+// The descriptor with its device pointers cleared (the part a checkpoint
+// compares).
+Desc portable_desc(const Desc& D) {
+  Desc P;
+  std::memcpy(&P, &D, sizeof(Desc));
+  P.u = P.du = P.z = P.dz = P.xz = P.az = nullptr;
+  P.sc = nullptr;
+  return P;
+}
+
+size_t ckpt_state_offset(const sfd_string* s) {
+  return static_cast<size_t>(reinterpret_cast<const char*>(s->d_sc) - s->block);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1049,6 +1145,8 @@ sfd_status sfd_excite_pluck(sfd_string* s, double amp_m, double pos) {
   s->pluck_amp = amp_m;
   s->pluck_pos = pos;
   fill_desc(s);
+  clear_excitation(s->h);
+  record_excitation(s, kPluck, {amp_m, pos, 0.0, 0.0, 0.0, 0.0});
   sfd_status rc = set_device(s->ctx);
   if (rc) return rc;
   stage_initial(s);
@@ -1064,6 +1162,8 @@ sfd_status sfd_excite_hammer(sfd_string* s, double mass_kg, double vel_mps, doub
   const sfd_string_params& p = s->p;
   s->exc = kHammer;
   fill_desc(s);
+  clear_excitation(s->h);
+  record_excitation(s, kHammer, {mass_kg, vel_mps, pos, omega_h, alpha_h, 0.0});
   point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
   s->exc_pos = pos;
   s->h.ham_M = static_cast<float>(mass_kg / (p.linear_density * p.length_m));
@@ -1088,6 +1188,8 @@ sfd_status sfd_excite_bow(sfd_string* s, double vel_mps, double force_n, double 
   s->exc = kBow;
   s->pluck_amp = 0;
   fill_desc(s);
+  clear_excitation(s->h);
+  record_excitation(s, kBow, {vel_mps, force_n, pos, a_s_per_m, eps, release_time_s});
   point_weights(s->n_t, pos, &s->h.e_node, &s->h.e_w);
   s->exc_pos = pos;
   s->h.bow_F = static_cast<float>(force_n / (p.linear_density * p.length_m * p.length_m));
@@ -1146,6 +1248,11 @@ sfd_status sfd_bow_envelope(sfd_string* s, int32_t n_points, const double* t_s, 
   if (s->started) return fail(SFD_ESTATE, "set the bow envelope before synthesizing");
   sfd_status rc = apply_bow_envelope(s, n_points, t_s, vel_mps, force_n, pos);
   if (rc) return rc;
+  s->rec_env_n = n_points;
+  s->rec_env_mask = (vel_mps ? 1 : 0) | (force_n ? 2 : 0) | (pos ? 4 : 0);
+  const double* src[4] = {t_s, vel_mps, force_n, pos};
+  for (int c = 0; c < 4; ++c)
+    for (int j = 0; j < 16; ++j) s->rec_env[c][j] = (src[c] && j < n_points) ? src[c][j] : 0.0;
   stage_initial(s);
   return SFD_OK;
 }
@@ -1158,6 +1265,7 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
   if (!(peak > s->p.f0_max_ratio * (1.0 + 1e-12))) {
     sfd_status rc = apply_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
     if (rc) return rc;
+    record_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
     stage_initial(s);
     return SFD_OK;
   }
@@ -1183,6 +1291,7 @@ sfd_status sfd_set_modulation(sfd_string* s, int32_t kind, double rate_hz, doubl
   c->pool.dealloc(saved.block);
   s->block = nb;
   carve(s);
+  record_modulation(s, kind, rate_hz, depth, phase_rad, duration_s);
   stage_initial(s);
   return SFD_OK;
 }
@@ -1315,6 +1424,127 @@ sfd_status sfd_string_destroy(sfd_string* s) {
   if (set_device(c) == SFD_OK) cudaStreamSynchronize(c->stream);
   c->pool.dealloc(s->block);
   delete s;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_save(const sfd_string* s, void* buf, size_t* bytes) {
+  if (!s || !bytes) return fail(SFD_EINVAL, "NULL argument");
+  const size_t state_off = ckpt_state_offset(s);
+  const size_t state_bytes = block_bytes(s->h) - state_off;
+  const size_t fixed = sizeof(CkptHeader) + sizeof(CkptRecord) + sizeof(Desc);
+  const size_t total = fixed + state_bytes;
+  if (!buf) {
+    *bytes = total;
+    return SFD_OK;
+  }
+  if (*bytes < total) {
+    const size_t have = *bytes;
+    *bytes = total;
+    return fail(SFD_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", have, total);
+  }
+  sfd_status rc = set_device(s->ctx);
+  if (rc) return rc;
+  if ((rc = flush_string(s))) return rc;
+  char* out = static_cast<char*>(buf);
+  SFD_CUDA(d2h(s->ctx, out + fixed, s->block + state_off, state_bytes));
+  SFD_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  CkptHeader H{};
+  std::memcpy(H.magic, kCkptMagic, sizeof(H.magic));
+  H.version = kCkptVersion;
+  H.header_bytes = sizeof(CkptHeader);
+  H.total_bytes = total;
+  H.params_bytes = sizeof(sfd_string_params);
+  H.desc_bytes = sizeof(Desc);
+  H.scalars_bytes = sizeof(Scalars);
+  H.record_bytes = sizeof(CkptRecord);
+  H.state_offset = state_off;
+  H.state_bytes = state_bytes;
+  H.n_t = s->n_t;
+  H.n_l = s->n_l;
+  H.started = s->started ? 1 : 0;
+  CkptRecord R{};
+  R.p = s->p;
+  R.exc = s->rec_exc;
+  R.env_n = s->rec_env_n;
+  R.env_mask = s->rec_env_mask;
+  R.mod = s->rec_mod;
+  std::memcpy(R.exc_args, s->rec_exc_args, sizeof(R.exc_args));
+  std::memcpy(R.env, s->rec_env, sizeof(R.env));
+  std::memcpy(R.mod_args, s->rec_mod_args, sizeof(R.mod_args));
+  const Desc P = portable_desc(s->h);
+  std::memcpy(out, &H, sizeof(H));
+  std::memcpy(out + sizeof(H), &R, sizeof(R));
+  std::memcpy(out + sizeof(H) + sizeof(R), &P, sizeof(Desc));
+  *bytes = total;
+  return SFD_OK;
+}
+
+sfd_status sfd_string_load(sfd_ctx* c, const void* buf, size_t bytes, sfd_string** out) {
+  if (!c || !buf || !out) return fail(SFD_EINVAL, "NULL argument");
+  *out = nullptr;
+  const size_t fixed = sizeof(CkptHeader) + sizeof(CkptRecord) + sizeof(Desc);
+  if (bytes < fixed) return fail(SFD_EINVAL, "checkpoint truncated (%zu bytes)", bytes);
+  const char* in = static_cast<const char*>(buf);
+  CkptHeader H;
+  std::memcpy(&H, in, sizeof(H));
+  if (std::memcmp(H.magic, kCkptMagic, sizeof(H.magic)) != 0) return fail(SFD_EINVAL, "not a string checkpoint");
+  if (H.version != kCkptVersion || H.header_bytes != sizeof(CkptHeader) || H.params_bytes != sizeof(sfd_string_params) ||
+      H.desc_bytes != sizeof(Desc) || H.scalars_bytes != sizeof(Scalars) || H.record_bytes != sizeof(CkptRecord))
+    return fail(SFD_EINVAL, "checkpoint written by another version of the library");
+  if (H.total_bytes != bytes || H.state_bytes != bytes - fixed)
+    return fail(SFD_EINVAL, "checkpoint size does not match its header");
+  CkptRecord R;
+  std::memcpy(&R, in + sizeof(H), sizeof(R));
+  Desc saved;
+  std::memcpy(&saved, in + sizeof(H) + sizeof(R), sizeof(Desc));
+  Scalars sc;
+  if (H.state_bytes < sizeof(Scalars)) return fail(SFD_EINVAL, "checkpoint state truncated");
+  std::memcpy(&sc, in + fixed, sizeof(Scalars));
+  if (sc.n < 1 || sc.next_out < sc.n - 1 || sc.next_out > sc.n + 1)
+    return fail(SFD_EINVAL, "checkpoint time level %lld / next sample %lld inconsistent",
+                static_cast<long long>(sc.n), static_cast<long long>(sc.next_out));
+  if (R.env_n < 0 || R.env_n > 16) return fail(SFD_EINVAL, "checkpoint bow envelope has %d breakpoints", R.env_n);
+
+  // replay the set-up calls (each validates its arguments)
+  sfd_string* s = nullptr;
+  sfd_status rc = sfd_string_create(c, &R.p, &s);
+  if (rc) return rc;
+  const double* a = R.exc_args;
+  if (R.exc == kPluck) rc = sfd_excite_pluck(s, a[0], a[1]);
+  else if (R.exc == kHammer) rc = sfd_excite_hammer(s, a[0], a[1], a[2], a[3], a[4]);
+  else if (R.exc == kBow) rc = sfd_excite_bow(s, a[0], a[1], a[2], a[3], a[4], a[5]);
+  else rc = fail(SFD_EINVAL, "checkpoint excitation kind %d", R.exc);
+  if (rc == SFD_OK && R.env_n > 0)
+    rc = sfd_bow_envelope(s, R.env_n, R.env[0], (R.env_mask & 1) ? R.env[1] : nullptr,
+                          (R.env_mask & 2) ? R.env[2] : nullptr, (R.env_mask & 4) ? R.env[3] : nullptr);
+  if (rc == SFD_OK && R.mod != SFD_MOD_NONE)
+    rc = sfd_set_modulation(s, R.mod, R.mod_args[0], R.mod_args[1], R.mod_args[2], R.mod_args[3]);
+  if (rc) {
+    std::string why = sfd_last_error();
+    sfd_string_destroy(s);
+    return fail(SFD_EINVAL, "checkpoint set-up does not replay: %s", why.c_str());
+  }
+  const Desc rebuilt = portable_desc(s->h);
+  if (s->n_t != H.n_t || s->n_l != H.n_l || std::memcmp(&rebuilt, &saved, sizeof(Desc)) != 0 ||
+      ckpt_state_offset(s) != H.state_offset || block_bytes(s->h) - ckpt_state_offset(s) != H.state_bytes) {
+    sfd_string_destroy(s);
+    return fail(SFD_EINVAL,
+                "checkpoint descriptor differs from the one its parameters give here (another build or host)");
+  }
+  // the descriptor as rebuilt (with this block's pointers) and the saved state
+  if ((rc = set_device(c)) == SFD_OK) {
+    cudaError_t e = h2d(c, s->d_desc, &s->h, sizeof(Desc));
+    if (e == cudaSuccess) e = h2d(c, s->block + H.state_offset, in + fixed, H.state_bytes);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "checkpoint upload");
+  }
+  if (rc) {
+    sfd_string_destroy(s);
+    return rc;
+  }
+  s->dirty = false;
+  s->started = H.started != 0;
+  *out = s;
   return SFD_OK;
 }
 

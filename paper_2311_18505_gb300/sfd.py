@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
         "sfd_string_stats": (i32, [vp, P(i32), P(i32), P(i64)]),
         "sfd_string_delta_state": (i32, [vp, vp, vp, vp, vp]),
         "sfd_string_hammer": (i32, [vp, P(dbl), P(dbl)]),
+        "sfd_string_save": (i32, [vp, vp, P(ctypes.c_size_t)]),
+        "sfd_string_load": (i32, [vp, vp, ctypes.c_size_t, P(vp)]),
         "sfd_ctx_set_sweep_cap": (i32, [vp, i32]),
         "sfd_batch_create": (i32, [vp, i32, P(vp), P(vp)]),
         "sfd_batch_synthesize": (i32, [vp, P(i64), vp, P(i64), P(i32)]),
@@ -291,6 +293,22 @@ def sfd_string_hammer(s: int) -> tuple[float, float]:
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().sfd_string_hammer(s, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def sfd_string_save(s: int) -> bytes:
+    """Checkpoint of a string (state, parameters and set-up calls)."""
+    n = ctypes.c_size_t()
+    _check(lib().sfd_string_save(s, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().sfd_string_save(s, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def sfd_string_load(ctx: int, blob: bytes) -> int:
+    """A new string in ctx that continues the checkpointed one."""
+    h = ctypes.c_void_p()
+    _check(lib().sfd_string_load(ctx, blob, len(blob), ctypes.byref(h)))
+    return h.value
 
 
 def sfd_string_stats(s: int) -> tuple[int, int, int]:
