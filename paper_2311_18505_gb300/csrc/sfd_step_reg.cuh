@@ -100,9 +100,15 @@ __device__ __forceinline__ void tri_factor_r(const float (&sb)[MU], float (&iv)[
     ff[r] = -cp[r] * ff[r + 1];
     gg[r] = -al[r] - cp[r] * gg[r + 1];
   }
-  float f0n = __shfl_down_sync(SFD_FULL, ff[0], 1);
-  float g0n = __shfl_down_sync(SFD_FULL, gg[0], 1);
-  if (lane == kWarp - 1) { f0n = 0.f; g0n = 0.f; }
+  float f0n, g0n;
+  if (MU == 1) {   // one row per lane: every lane's ff = 1, gg = 0
+    f0n = lane == kWarp - 1 ? 0.f : 1.f;
+    g0n = 0.f;
+  } else {
+    f0n = __shfl_down_sync(SFD_FULL, ff[0], 1);
+    g0n = __shfl_down_sync(SFD_FULL, gg[0], 1);
+    if (lane == kWarp - 1) { f0n = 0.f; g0n = 0.f; }
+  }
   const float cl = cp[MU - 1];
   float A = al[MU - 1], B = 1.f + cl * g0n, C = cl * f0n;
   rd.cl = cl;
@@ -155,9 +161,14 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
     x1[r] = x1[r] - cp[r] * x1[r + 1];
     if (NR == 2) x2[r] = x2[r] - cp[r] * x2[r + 1];
   }
-  float e1 = __shfl_down_sync(SFD_FULL, x1[0], 1);
-  float e2 = NR == 2 ? __shfl_down_sync(SFD_FULL, x2[0], 1) : 0.f;
-  if (lane == kWarp - 1) { e1 = 0.f; e2 = 0.f; }
+  // (one row per lane: the row just cleared is the neighbour's first, so
+  // e1 = e2 = 0 and the shuffles are skipped)
+  float e1 = 0.f, e2 = 0.f;
+  if (MU > 1) {
+    e1 = __shfl_down_sync(SFD_FULL, x1[0], 1);
+    e2 = NR == 2 ? __shfl_down_sync(SFD_FULL, x2[0], 1) : 0.f;
+    if (lane == kWarp - 1) { e1 = 0.f; e2 = 0.f; }
+  }
   float D1 = dl1 - rd.cl * e1, D2 = dl2 - rd.cl * e2;
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
@@ -175,9 +186,13 @@ __device__ __forceinline__ void tri_solve_r(const float (&sb)[MU], const float (
     if (NR == 2) D2 = D2 - rd.k1[l] * m2 - rd.k2[l] * q2;
   }
   const float X1 = D1 * rd.binv, X2 = D2 * rd.binv;
-  float Xp1 = __shfl_up_sync(SFD_FULL, X1, 1);
-  float Xp2 = NR == 2 ? __shfl_up_sync(SFD_FULL, X2, 1) : 0.f;
-  if (lane == 0) { Xp1 = 0.f; Xp2 = 0.f; }
+  // (one row per lane: gg = 0, so the previous lane's unknown is not needed)
+  float Xp1 = 0.f, Xp2 = 0.f;
+  if (MU > 1) {
+    Xp1 = __shfl_up_sync(SFD_FULL, X1, 1);
+    Xp2 = NR == 2 ? __shfl_up_sync(SFD_FULL, X2, 1) : 0.f;
+    if (lane == 0) { Xp1 = 0.f; Xp2 = 0.f; }
+  }
 #pragma unroll
   for (int r = 0; r < MU; ++r) {
     x1[r] = x1[r] + ff[r] * X1 + gg[r] * Xp1;
@@ -344,6 +359,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   bool carry_ok = false;       // the lane's first interval began in an earlier lane
   bool scan_flag = true;       // the lane's last interval begins in this lane
   int scan_lv = 0;             // shuffle levels that close every interval
+  unsigned scan_add = 0;       // bit l: the lane adds the sum from lane - 2^l at scan level l
   if (has_z) {
 #pragma unroll
     for (int r = 0; r < MU; ++r) { mmr[r] = TMIs[ub + r]; wr[r] = TMWs[ub + r]; }
@@ -362,7 +378,10 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
     for (int l = 0; l < 5 && !__all_sync(SFD_FULL, f); ++l) {
       const int sh = 1 << l;
       const bool fu = __shfl_up_sync(SFD_FULL, f ? 1 : 0, sh) != 0;
-      if (lane >= sh) f = f || fu;
+      if (lane >= sh) {
+        if (!f) scan_add |= 1u << l;
+        f = f || fu;
+      }
       scan_lv = l + 1;
     }
   }
@@ -389,7 +408,6 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
       b1[r] = cont ? b1[r > 0 ? r - 1 : 0] + q1 : q1;
     }
     float v0 = a0[MU - 1], v1 = a1[MU - 1], x0 = b0[MU - 1], x1 = b1[MU - 1];
-    bool fl = scan_flag;
 #pragma unroll
     for (int l = 0; l < 5; ++l) {
       if (l >= scan_lv) break;
@@ -400,11 +418,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
         y0 = __shfl_up_sync(SFD_FULL, x0, sh);
         y1 = __shfl_up_sync(SFD_FULL, x1, sh);
       }
-      const bool fu = __shfl_up_sync(SFD_FULL, fl ? 1 : 0, sh) != 0;
-      if (lane >= sh) {
-        if (!fl) { v0 += u0; v1 += u1; x0 += y0; x1 += y1; }
-        fl = fl || fu;
-      }
+      if ((scan_add >> l) & 1u) { v0 += u0; v1 += u1; x0 += y0; x1 += y1; }
     }
     float c0 = __shfl_up_sync(SFD_FULL, v0, 1), c1 = __shfl_up_sync(SFD_FULL, v1, 1);
     float d0 = 0.f, d1 = 0.f;
@@ -745,8 +759,9 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
             }
             xpar ^= 1;
           }
-          float el = chg > 0.f ? chg / fmaxf(mag, scz) : 0.f;
-          if (need_resp) el = fmaxf(el, chx > 0.f ? chx / fmaxf(mgx, scx) : 0.f);
+          // (a measure compared with thresholds: the fast divide suffices)
+          float el = chg > 0.f ? __fdividef(chg, fmaxf(mag, scz)) : 0.f;
+          if (need_resp) el = fmaxf(el, chx > 0.f ? __fdividef(chx, fmaxf(mgx, scx)) : 0.f);
           mag_all = fmaxf(mag_all, mag);
           mgx_all = fmaxf(mgx_all, mgx);
           const float e = warp_max_nonneg(el);

@@ -363,7 +363,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
           mgx = warp_max_nonneg(mgx);
           __syncwarp();
           ++sweep;
-          const float e = fmaxf(chg > 0.f ? chg / mag : 0.f, chx > 0.f ? chx / mgx : 0.f);
+          const float e = fmaxf(chg > 0.f ? __fdividef(chg, mag) : 0.f, chx > 0.f ? __fdividef(chx, mgx) : 0.f);
           if (sweep_converged(e, e_prev, sweep)) break;
           if (sweep >= sweep_cap) { status |= kStNoConv; break; }
           e_prev = e;

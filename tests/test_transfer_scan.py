@@ -60,12 +60,17 @@ def scan_transfer(n_t: int, n_l: int, mu: int, f: np.ndarray, cross_lane: bool =
                 lastm[l] &= ~(1 << r)        # pad rows store nothing
         carry_ok[l] = l > 0 and prv[l] == mmr[l][0]
         flag[l] = not (l > 0 and prv[l] == mmr[l][mu - 1])
-    fs, levels = list(flag), 0
+    # levels that close every interval, and per lane the levels at which it
+    # adds the partial sum from lane - 2^level (computed once per job)
+    fs, levels, add_mask = list(flag), 0, [0] * W
     for lv in range(5):
         if all(fs):
             break
         sh = 1 << lv
         fu = shfl_up(fs, sh)
+        for l in range(W):
+            if l >= sh and not fs[l]:
+                add_mask[l] |= 1 << lv
         fs = [fs[l] or fu[l] if l >= sh else fs[l] for l in range(W)]
         levels = lv + 1
     assert all(fs)
@@ -80,16 +85,13 @@ def scan_transfer(n_t: int, n_l: int, mu: int, f: np.ndarray, cross_lane: bool =
             a1[l][r] = a1[l][r - 1] + p1 if cont else p1
     v0 = [a0[l][mu - 1] for l in range(W)]
     v1 = [a1[l][mu - 1] for l in range(W)]
-    fg = list(flag)
     for lv in range(levels if cross_lane else 0):
         sh = 1 << lv
-        u0, u1, fu = shfl_up(v0, sh), shfl_up(v1, sh), shfl_up(fg, sh)
+        u0, u1 = shfl_up(v0, sh), shfl_up(v1, sh)
         for l in range(W):
-            if l >= sh:
-                if not fg[l]:
-                    v0[l] += u0[l]
-                    v1[l] += u1[l]
-                fg[l] = fg[l] or fu[l]
+            if (add_mask[l] >> lv) & 1:
+                v0[l] += u0[l]
+                v1[l] += u1[l]
     c0, c1 = shfl_up(v0, 1), shfl_up(v1, 1)
     if not cross_lane:
         c0, c1 = [0.0] * W, [0.0] * W
