@@ -455,13 +455,18 @@ sfd_status sfd_server_destroy(sfd_server* sv);
  * the pluck amp_m, the hammer vel_mps, or the bow velocity vel_mps.  The
  * gradient is that of the discrete scheme on the string's grid (N_t, N_l
  * held fixed), through the FP32 trajectory the forward computed: each
- * segment between checkpoints is replayed from its checkpoint and swept
- * backwards by the adjoint kernel.  For a bowed string each step keeps the
+ * segment between checkpoints is swept backwards by the adjoint kernel over
+ * its levels, which the forward recorded (when the whole trajectory, n x
+ * n_samples x (2 (N_t - 1) + 2 (N_l - 1) + 2) floats rounded up, fits in
+ * 4 GiB and the device has room; see sfd_tape_set_record_forward) or which
+ * are replayed from the segment's checkpoint (the same values bit for
+ * bit).  For a bowed string each step keeps the
  * regime (sliding or sticking, Sec. 3.3.1) the forward took: the loss is
  * piecewise smooth in the parameters, and this is its derivative between
  * regime switches.
  * The tape's own device memory (checkpoints, one segment's replay record,
- * adjoint state) is allocated at create; the strings come from the ctx pool.
+ * the whole-trajectory record when it is kept, adjoint state) is allocated
+ * at create; the strings come from the ctx pool.
  * --------------------------------------------------------------------- */
 typedef struct sfd_tape sfd_tape;
 #define SFD_GRAD_PARAMS 5
@@ -479,6 +484,13 @@ sfd_status sfd_tape_create(sfd_ctx* ctx, int32_t n, const sfd_string_params* par
 sfd_status sfd_tape_forward(sfd_tape* t, float* y_device);
 /* SFD_ESTATE before a forward. */
 sfd_status sfd_tape_backward(sfd_tape* t, const float* dy_device, double* grad);
+/* Record every level on the forward pass (enable = 1: the backward replays
+ * nothing; SFD_ENOMEM when the device has no room for the record, whatever
+ * its size) or replay each segment from its checkpoint (enable = 0: the
+ * record's device memory is freed).  Enabling invalidates an earlier forward
+ * pass (sfd_tape_backward then returns SFD_ESTATE until the next forward).
+ * The gradients are the same bit for bit either way. */
+sfd_status sfd_tape_set_record_forward(sfd_tape* t, int32_t enable);
 sfd_status sfd_tape_destroy(sfd_tape* t);
 
 /* Throughput peaks of device `device`, measured by three short

@@ -3,7 +3,11 @@
 // that, segment by segment from the last, restores a replay copy of each
 // string from the segment's checkpoint, re-runs the forward kernels over the
 // segment recording every level (Job::traj), and runs the adjoint kernel
-// (sfd_adjoint.cu) backwards over those levels.
+// (sfd_adjoint.cu) backwards over those levels.  When the whole trajectory
+// fits (kRecordForwardBytes, or sfd_tape_set_record_forward), the forward
+// kernels record every level as they go and the reverse sweep replays
+// nothing: a replay re-runs the same kernel from the same state, so its
+// record is the forward's, bit for bit.
 //
 // Included once, at the end of sfd_api.cu (uses its internal pieces).
 
@@ -14,6 +18,8 @@ cudaError_t launch_adjoint(const AdjJob* d_jobs, int n_jobs, int smem_bytes, cud
 namespace {
 
 constexpr size_t kTapeAlign = 256;
+// largest whole-trajectory record the tape allocates on its own
+constexpr size_t kRecordForwardBytes = size_t{4} << 30;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -38,6 +44,7 @@ struct sfd_tape {
   float* d_scratch = nullptr;
   AdjJob* d_ajobs = nullptr;
   bool forward_done = false;
+  float* d_traj_full = nullptr;         // every level of every segment (record-on-forward mode)
 };
 
 namespace {
@@ -56,7 +63,17 @@ void tape_free(sfd_tape* t) {
   cudaFree(t->d_grad);
   cudaFree(t->d_scratch);
   cudaFree(t->d_ajobs);
+  cudaFree(t->d_traj_full);
   delete t;
+}
+
+size_t full_traj_bytes(const sfd_tape* t) {
+  return sizeof(float) * static_cast<size_t>(t->n) * t->n_seg * t->traj_stride;
+}
+
+// segment seg of string i in the whole-trajectory record
+float* full_traj(const sfd_tape* t, int i, int seg) {
+  return t->d_traj_full + (static_cast<size_t>(i) * t->n_seg + seg) * t->traj_stride;
 }
 
 char* ckpt_slot(const sfd_tape* t, int i, int c) {
@@ -136,11 +153,40 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
     if (e == cudaSuccess) e = cudaMalloc(&t->d_ajobs, sizeof(AdjJob) * n);
     if (e != cudaSuccess) rc = cuda_fail(e, "tape buffers");
   }
+  if (rc == SFD_OK && full_traj_bytes(t) <= kRecordForwardBytes) {
+    // record on the forward pass when the device has room; else replay
+    if (cudaMalloc(&t->d_traj_full, full_traj_bytes(t)) != cudaSuccess) {
+      t->d_traj_full = nullptr;
+      cudaGetLastError();   // an allocation failure is not sticky: clear it
+    }
+  }
   if (rc) {
     tape_free(t);
     return rc;
   }
   *out = t;
+  return SFD_OK;
+}
+
+sfd_status sfd_tape_set_record_forward(sfd_tape* t, int32_t enable) {
+  if (!t) return fail(SFD_EINVAL, "NULL argument");
+  sfd_status rc = set_device(t->c);
+  if (rc) return rc;
+  if (!enable) {
+    if (t->d_traj_full) {
+      SFD_CUDA(cudaStreamSynchronize(t->c->stream));
+      cudaFree(t->d_traj_full);
+      t->d_traj_full = nullptr;
+    }
+    return SFD_OK;
+  }
+  if (t->d_traj_full) return SFD_OK;
+  if (cudaMalloc(&t->d_traj_full, full_traj_bytes(t)) != cudaSuccess) {
+    t->d_traj_full = nullptr;
+    cudaGetLastError();
+    return fail(SFD_ENOMEM, "no device room for the %zu-byte trajectory record", full_traj_bytes(t));
+  }
+  t->forward_done = false;   // the next forward pass records
   return SFD_OK;
 }
 
@@ -159,7 +205,14 @@ sfd_status sfd_tape_forward(sfd_tape* t, float* y_device) {
     const int64_t first = static_cast<int64_t>(seg) * t->K;
     const int64_t ns = std::min<int64_t>(t->K, t->n_samples - first);
     std::vector<Job> jobs;
-    for (int i = 0; i < t->n; ++i) jobs.push_back(Job{t->fw[i]->d_desc, y_device + i * t->n_samples + first, ns});
+    for (int i = 0; i < t->n; ++i) {
+      Job j{t->fw[i]->d_desc, y_device + i * t->n_samples + first, ns};
+      if (t->d_traj_full) {
+        j.traj = full_traj(t, i, seg);
+        j.traj_stride = t->rec_stride[i];
+      }
+      jobs.push_back(j);
+    }
     if ((rc = launch_jobs(c, jobs, owners))) return rc;
     for (sfd_string* s : t->fw) s->started = true;
     if ((rc = tape_checkpoint(t, t->fw, seg + 1))) return rc;
@@ -192,17 +245,19 @@ sfd_status sfd_tape_backward(sfd_tape* t, const float* dy_device, double* grad) 
     const int64_t first = static_cast<int64_t>(seg) * t->K;
     const int64_t ns = std::min<int64_t>(t->K, t->n_samples - first);
     const int64_t m0 = seg_start_level(t, seg), m1 = first + ns - 1;
-    // replay the segment from its checkpoint, recording every level
+    // the segment's levels: recorded by the forward pass, or replayed now
+    // from the segment's checkpoint
     std::vector<Job> jobs;
     for (int i = 0; i < t->n; ++i) {
-      SFD_CUDA(cudaMemcpyAsync(t->rp[i]->block + t->st_off[i], ckpt_slot(t, i, seg), t->st_bytes[i],
-                               cudaMemcpyDeviceToDevice, c->stream));
       Job j{t->rp[i]->d_desc, t->d_scratch + static_cast<size_t>(i) * t->K, ns};
-      j.traj = t->d_traj + static_cast<size_t>(i) * t->traj_stride;
+      j.traj = t->d_traj_full ? full_traj(t, i, seg) : t->d_traj + static_cast<size_t>(i) * t->traj_stride;
       j.traj_stride = t->rec_stride[i];
       jobs.push_back(j);
+      if (!t->d_traj_full)
+        SFD_CUDA(cudaMemcpyAsync(t->rp[i]->block + t->st_off[i], ckpt_slot(t, i, seg), t->st_bytes[i],
+                                 cudaMemcpyDeviceToDevice, c->stream));
     }
-    if ((rc = launch_jobs(c, jobs, owners))) return rc;
+    if (!t->d_traj_full && (rc = launch_jobs(c, jobs, owners))) return rc;
     // reverse sweep over the segment's levels (m0, m1]
     for (int i = 0; i < t->n; ++i) {
       const sfd_string* s = t->rp[i];

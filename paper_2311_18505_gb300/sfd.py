@@ -154,6 +154,7 @@ def lib() -> ctypes.CDLL:
         "sfd_tape_forward": (i32, [vp, vp]),
         "sfd_tape_backward": (i32, [vp, vp, P(dbl)]),
         "sfd_tape_destroy": (i32, [vp]),
+        "sfd_tape_set_record_forward": (i32, [vp, i32]),
         "sfd_measure_peaks": (i32, [ctypes.c_int, P(dbl), P(dbl), P(dbl)]),
         "sfd_last_error": (ctypes.c_char_p, []),
     }
@@ -572,6 +573,11 @@ def sfd_tape_backward(tape: int, dy_device, n: int) -> np.ndarray:
     g = np.zeros((n, SFD_GRAD_PARAMS), dtype=np.float64)
     _check(lib().sfd_tape_backward(tape, ptr, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return g
+
+
+def sfd_tape_set_record_forward(tape: int, enable: bool) -> None:
+    """Record every level on the forward pass (True) or replay segments (False)."""
+    _check(lib().sfd_tape_set_record_forward(tape, 1 if enable else 0))
 
 
 def sfd_tape_destroy(tape: int) -> None:

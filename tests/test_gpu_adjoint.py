@@ -50,9 +50,11 @@ def targets_of(target, n):
     return np.stack(ys)
 
 
-def adjoint_grad(sfd, ctx, base, tgt, n, K=1024):
+def adjoint_grad(sfd, ctx, base, tgt, n, K=1024, record=None):
     tape = sfd.sfd_tape_create(ctx, base, n, K)
     try:
+        if record is not None:
+            sfd.sfd_tape_set_record_forward(tape, record)
         y = torch.empty(len(base), n, device="cuda", dtype=torch.float32)
         sfd.sfd_tape_forward(tape, y)
         dy = 2.0 * (y.double() - torch.from_numpy(tgt).cuda())
@@ -357,6 +359,39 @@ def test_gradient_does_not_depend_on_the_checkpoint_interval(sfd, ctx):
     # grouping of the FP64 gradient sums differs
     np.testing.assert_allclose(g2, g1, rtol=1e-9, atol=0)
     np.testing.assert_allclose(g3, g1, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("K", [1024, 333])
+def test_recorded_forward_equals_replayed_segments(sfd, ctx, K):
+    """The backward pass over levels the forward pass recorded gives the
+    gradient of the one that replays each segment from its checkpoint, bit
+    for bit (a replay re-runs the same kernel from the same state)."""
+    base, target = workload(6, N_SHORT)
+    tgt = targets_of(target, N_SHORT)
+    g_rec, y_rec = adjoint_grad(sfd, ctx, base, tgt, N_SHORT, K=K, record=True)
+    g_rep, y_rep = adjoint_grad(sfd, ctx, base, tgt, N_SHORT, K=K, record=False)
+    assert np.array_equal(y_rec, y_rep)
+    assert np.array_equal(g_rec, g_rep)
+
+
+def test_record_forward_invalidates_an_earlier_forward(sfd, ctx):
+    """Switching the tape to recording after a forward pass asks for a new
+    forward pass before the backward (SFD_ESTATE)."""
+    base, target = workload(2, 2000)
+    tape = sfd.sfd_tape_create(ctx, base, 2000, 512)
+    try:
+        sfd.sfd_tape_set_record_forward(tape, False)
+        y = torch.empty(2, 2000, device="cuda", dtype=torch.float32)
+        sfd.sfd_tape_forward(tape, y)
+        sfd.sfd_tape_set_record_forward(tape, True)
+        with pytest.raises(sfd.SfdError) as e:
+            sfd.sfd_tape_backward(tape, torch.zeros_like(y), 2)
+        assert e.value.code == sfd.SFD_ESTATE
+        sfd.sfd_tape_forward(tape, y)
+        g = sfd.sfd_tape_backward(tape, torch.zeros_like(y), 2)
+        assert np.all(g == 0.0)
+    finally:
+        sfd.sfd_tape_destroy(tape)
 
 
 def test_autograd_function_and_a_descent_step(sfd, ctx):
