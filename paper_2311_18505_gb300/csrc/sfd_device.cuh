@@ -206,7 +206,9 @@ __device__ __forceinline__ float mod_factor(int kind, uint64_t inc_fx, uint64_t 
   if (kind == 1) {
     const uint64_t t_fx = static_cast<uint64_t>(n) * inc_fx + phase_fx;
     const float t = static_cast<float>(static_cast<uint32_t>(t_fx >> 40)) * 5.9604644775390625e-8f;   // 2^-24
-    return exp2f(depth2 * sinf(6.28318530717958647f * t));
+    // sin(2 pi t) = -sin(2 pi (t - 1/2)), whose argument lies in [-pi, pi):
+    // there the hardware sine's absolute error is ~2^-21, i.e. ~1e-8 in rm
+    return exp2f(-depth2 * __sinf(6.28318530717958647f * (t - 0.5f)));
   }
   if (kind == 2) return exp2f(n < n_end ? inc * static_cast<float>(n) : hold);
   return 1.f;
@@ -253,7 +255,7 @@ __device__ __forceinline__ float bow_phi(float b, float c, float a, float eps, f
     const float w = fabsf(b);
     return b == 0.f ? 0.f : copysignf(eps + (1.f - eps) * expf(-a * w), b);
   }
-  if (fabsf(b) <= c) return b / c;
+  if (fabsf(b) <= c) return __fdividef(b, c);   // |b| <= c, c > 0: within 2 ulp
   const float B = fabsf(b);
   const float a2 = a * 1.44269504088896341f;   // e^{-a w} = 2^{-a2 w}
   const float ce = c * (1.f - eps), c0 = c * eps - B;

@@ -280,6 +280,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
   const float ham_k2w = Dp->ham_k2w, ham_expo = Dp->ham_expo, ham_M = Dp->ham_M;
   const float bow_F = Dp->bow_F, bow_v = Dp->bow_v, bow_a = Dp->bow_a, bow_eps = Dp->bow_eps;
   const float kk = Dp->k, k2 = Dp->k2;
+  const float inv2k = 0.5f / kk;   // 1 / 2k: the bow's velocity I(a + 2D) / 2k without a divide per step
   const int64_t bow_release_n = Dp->bow_release_n;
   const int sweep_cap = job.sweep_cap > 0 ? job.sweep_cap : kMaxSweeps;
 
@@ -793,7 +794,7 @@ __device__ void run_job_reg(const Job& job, float* __restrict__ wbase, int lane,
           if (has_z) z_axpy(s);
         }
       } else if (exc == kBow && FB > 0.f) {
-        const float b = (node_interp<MU>(AC, en, ew, n_u) + 2.f * node_interp<MU>(DU, en, ew, n_u)) / (2.f * kk) -
+        const float b = (node_interp<MU>(AC, en, ew, n_u) + 2.f * node_interp<MU>(DU, en, ew, n_u)) * inv2k -
                         bv;
         const float c = 0.5f * kk * FB * node_interp<MU>(XP, en, ew, n_u);
         const float phi = bow_phi(b, c, bow_a, bow_eps, bow_w);

@@ -389,7 +389,7 @@ static __device__ void run_job(const Job& job, float* __restrict__ wbase, int la
         }
       } else if (exc == kBow && FB > 0.f) {
         const float k = Dp->k;
-        const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) / (2.f * k) - bv;
+        const float b = (interp2(AC, en, ew) + 2.f * interp2(DU, en, ew)) * (0.5f / k) - bv;
         const float c = 0.5f * k * FB * interp2(XP, en, ew);
         const float phi = bow_phi(b, c, Dp->bow_a, Dp->bow_eps, bow_w);
         vrec = !(c > 0.f) ? b : (fabsf(b) <= c ? 0.f : b - c * phi);
