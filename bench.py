@@ -83,7 +83,7 @@ def algorithmic_flops(strings, grids, select=None, counts=None) -> float:
     return tot
 
 
-KERNEL_SOURCES = ["sfd_kernel.cu", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_types.h"]
+KERNEL_SOURCES = ["sfd_kernel.cu", "sfd_df64.cuh", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_types.h"]
 
 
 def kernel_sources_hash() -> str:

@@ -456,9 +456,10 @@ sfd_status sfd_server_destroy(sfd_server* sv);
  * gradient is that of the discrete scheme on the string's grid (N_t, N_l
  * held fixed), through the FP32 trajectory the forward computed: each
  * segment between checkpoints is swept backwards by the adjoint kernel over
- * its levels, which the forward recorded (when the whole trajectory, n x
- * n_samples x (2 (N_t - 1) + 2 (N_l - 1) + 2) floats rounded up, fits in
- * 4 GiB and the device has room; see sfd_tape_set_record_forward) or which
+ * its levels, which the forward recorded (when the whole trajectory, the
+ * sum over strings of n_samples x (2 (N_t - 1) + 2 (N_l - 1) + 2) floats,
+ * each count rounded up, fits in 4 GiB and the device has room; see
+ * sfd_tape_set_record_forward) or which
  * are replayed from the segment's checkpoint (the same values bit for
  * bit).  For a bowed string each step keeps the
  * regime (sliding or sticking, Sec. 3.3.1) the forward took: the loss is

@@ -26,7 +26,7 @@ UNITS = [("sfd_api.cu", "sfd_api.o", []), ("sfd_adjoint.cu", "sfd_adjoint.o", []
         [("sfd_kernel.cu", f"sfd_kernel_r{mu}.o", [f"-DSFD_MU={mu}"]) for mu in (1, 3, 5, 7, 9)] + \
         [("sfd_kernel.cu", "sfd_kernel_smem.o", [])]
 SOURCES = sorted({u[0] for u in UNITS})
-HEADERS = ["sfd_types.h", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_server.cuh",
+HEADERS = ["sfd_types.h", "sfd_df64.cuh", "sfd_device.cuh", "sfd_step_reg.cuh", "sfd_step_smem.cuh", "sfd_server.cuh",
            "sfd_tape.cuh"]
 
 

@@ -30,12 +30,18 @@
 // trajectory the forward produced.  One warp per string, every per-row
 // array in shared memory.
 //
-// The adjoint recursion runs in FP64 (the trajectory stays FP32): nu carries
-// a large smooth part, and its FP32 representation noise, amplified by the
-// second and fourth differences, enters L_u every step; after a few hundred
-// steps that noise dominates the adjoint's high-wavenumber content, which
-// is exactly what the kappa and sigma1 gradients weight (measured: 2-15 %
-// errors against the FP64 oracle's gradient in FP32, none in FP64).
+// The adjoint recursion runs in double-float arithmetic (sfd_df64.cuh,
+// ~48 bits; the trajectory stays FP32): nu carries a large smooth part, and
+// its FP32 representation noise, amplified by the second and fourth
+// differences, enters L_u every step; after a few hundred steps that noise
+// dominates the adjoint's high-wavenumber content, which is exactly what the
+// kappa and sigma1 gradients weight (measured: 2-15 % errors against the
+// oracle's gradient in FP32, none in FP64).  FP64 itself, at a small
+// fraction of the FP32 rate on this GPU, left each string's warp waiting on
+// the FP64 pipe; double-floats run on the FP32 pipes, and converting the
+// FP32 trajectory to them is free.  FP64 remains only at the segment
+// boundaries (the adjoint state kept between launches, the gradients) and
+// in the hammer's power law and the bow's friction exponential.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -46,21 +52,16 @@ namespace sfd {
 
 namespace {
 
-using R = double;
-constexpr R kAdjTol = 1e-13;     // relative change that ends an adjoint block Gauss-Seidel solve
+using R = df64;
+constexpr float kAdjTol = 1e-13f;   // relative change that ends an adjoint block Gauss-Seidel solve
 constexpr int kAdjSweeps = 40;
 
-__device__ __forceinline__ bool adj_converged(R e, R e_prev, int sweep) {
+// (the change measures e are float: they only decide when to stop)
+__device__ __forceinline__ bool adj_converged(float e, float e_prev, int sweep) {
   if (e <= kAdjTol) return true;
   if (sweep >= 2 && e < e_prev && e * e <= kAdjTol * e_prev) return true;
-  if (sweep >= 3 && e >= 0.5 * e_prev && e <= 64.0 * kAdjTol) return true;
+  if (sweep >= 3 && e >= 0.5f * e_prev && e <= 64.f * kAdjTol) return true;
   return sweep >= kAdjSweeps;
-}
-
-__device__ __forceinline__ R warp_max(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(SFD_FULL, v, o));
-  return v;
 }
 
 }  // namespace
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const int mod_kind = Dp->mod_kind;
   const float mod_depth2 = Dp->mod_depth2;
   R lam2 = static_cast<R>(lam2_0f) + static_cast<R>(lam2lo_0f), lam2l = lam2l_0f;
-  R ca = ca_0f, cb = cb_0f, cz = cz_0f, rmd = 1.0;
-  const R bsgn = Dp->boundary == 1 ? -1.0 : 1.0;
+  R ca = ca_0f, cb = cb_0f, cz = cz_0f, rmd = 1.0f;
+  const R bsgn = Dp->boundary == 1 ? -1.0f : 1.0f;
   const int en = Dp->e_node, on = Dp->o_node;
   const R ew = Dp->e_w, js = Dp->jscale, ow = Dp->o_w, oscale = Dp->out_scale;
   const bool zout = Dp->out_ch == 1;   // output reads zeta on the longitudinal grid
@@ -102,15 +103,16 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   const int64_t brel = Dp->bow_release_n;
 
   // ---- shared memory: FP64 adjoint arrays, then the FP32 trajectory ----
-  double* pd = smem_d;
-  auto DU_ = [&]() { double* a = pd + 2; pd += RU; return a; };
+  R* const rbase = reinterpret_cast<R*>(smem_d);   // double-floats: 8 bytes, as the FP64 slots
+  R* pd = rbase;
+  auto DU_ = [&]() { R* a = pd + 2; pd += RU; return a; };
   R *LU = DU_(), *LD = DU_(), *NA = DU_(), *RA = DU_(), *SUB = DU_(), *INV = DU_(), *CP = DU_(), *AL = DU_();
   R *FF = DU_(), *GG = DU_(), *XP = DU_(), *FT = DU_(), *PNZ = DU_(), *GAM = DU_(), *PSG = DU_(), *XZT = DU_();
   R* T1 = DU_();
   R *LZ = nullptr, *LDZ = nullptr, *NZ = nullptr, *RZ_ = nullptr, *SUBZ = nullptr, *INVZ = nullptr, *CPZ = nullptr;
   R *ALZ = nullptr, *FFZ = nullptr, *GGZ = nullptr, *E1Z = nullptr, *XZ = nullptr, *T2 = nullptr;
   if (has_z) {
-    auto DZ_ = [&]() { double* a = pd + 2; pd += RZ; return a; };
+    auto DZ_ = [&]() { R* a = pd + 2; pd += RZ; return a; };
     LZ = DZ_(); LDZ = DZ_(); NZ = DZ_(); RZ_ = DZ_(); SUBZ = DZ_(); INVZ = DZ_(); CPZ = DZ_(); ALZ = DZ_();
     FFZ = DZ_(); GGZ = DZ_(); E1Z = DZ_(); XZ = DZ_(); T2 = DZ_();
   }
@@ -128,8 +130,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     ZHI = reinterpret_cast<int*>(FZ_());
   }
   {
-    const int nd = static_cast<int>(pd - smem_d);
-    for (int k = lane; k < nd; k += kWarp) smem_d[k] = 0.0;
+    const int nd = static_cast<int>(pd - rbase);
+    for (int k = lane; k < nd; k += kWarp) smem_d[k] = 0.0f;
     float* f0 = reinterpret_cast<float*>(smem_d + nd);
     const int nf = static_cast<int>(pf - f0);
     for (int k = lane; k < nf; k += kWarp) f0[k] = 0.f;
@@ -154,19 +156,19 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     }
   }
   __syncwarp();
-  const R inv_nt = 1.0 / static_cast<R>(n_t);
+  const R inv_nt = 1.0f / static_cast<R>(n_t);
   auto interp_z = [&](const auto* X, int i) -> R {
     const int mm = TMI[i];
     const R w = TMW[i];
-    return (1.0 - w) * static_cast<R>(X[mm - 1]) + w * static_cast<R>(X[mm]);
+    return (1.0f - w) * static_cast<R>(X[mm - 1]) + w * static_cast<R>(X[mm]);
   };
   auto spread = [&](const R* F, int i) -> R {
     const int mm = i + 1, lo = ZLO[i], hi = ZHI[i];
-    R acc = 0.0;
+    R acc = 0.0f;
     for (int l = lo; l <= hi; ++l) {
       const int dd = l * n_l - mm * n_t;
-      const R w = 1.0 - static_cast<R>(dd < 0 ? -dd : dd) * inv_nt;
-      acc = fma(fmax(w, 0.0), F[l - 1], acc);
+      const R w = 1.0f - static_cast<R>(dd < 0 ? -dd : dd) * inv_nt;
+      acc = fma(fmax(w, 0.0f), F[l - 1], acc);
     }
     return acc;
   };
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   };
   auto d4_of = [&](const R* X, int i) -> R {
     const R gl = X[i] - X[i - 1], gr = X[i + 1] - X[i];
-    R d4 = ((X[i + 2] - X[i + 1]) - gr) - 2.0 * (gr - gl) + (gl - (X[i - 1] - X[i - 2]));
+    R d4 = ((X[i + 2] - X[i + 1]) - gr) - 2.0f * (gr - gl) + (gl - (X[i - 1] - X[i - 2]));
     if (i == 0) d4 += bsgn * X[i];
     if (i == n_u - 1) d4 += bsgn * X[i];
     return d4;
@@ -185,13 +187,13 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   // ---- constant matrices ----
   RedT<R> rdu, rdz;
   if (has_z) {
-    const R dzd = 1.0 + s0 + 2.0 * s1l;
+    const R dzd = 1.0f + s0 + 2.0f * s1l;
     for (int r = 0; r < m_z; ++r) {
       const int i = zb + r;
       const bool real = i < n_z;
-      SUBZ[i] = real && i > 0 ? -s1l : 0.0;
-      INVZ[i] = real ? dzd : 1.0;
-      CPZ[i] = real && i < n_z - 1 ? -s1l : 0.0;
+      SUBZ[i] = real && i > 0 ? -s1l : 0.0f;
+      INVZ[i] = real ? dzd : 1.0f;
+      CPZ[i] = real && i < n_z - 1 ? -s1l : 0.0f;
     }
     tri_factor(SUBZ, INVZ, CPZ, ALZ, FFZ, GGZ, m_z, lane, rdz);
   }
@@ -200,12 +202,12 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       const int i = ub + r;
       if (i < n_u) {
         const R gl = G[i], gr = G[i + 1];
-        const R gl2 = linear ? 0.0 : gl * gl, gr2 = linear ? 0.0 : gr * gr;
-        SUB[i] = i > 0 ? og - ca * gl2 : 0.0;
+        const R gl2 = linear ? 0.0f : gl * gl, gr2 = linear ? 0.0f : gr * gr;
+        SUB[i] = i > 0 ? og - ca * gl2 : 0.0f;
         INV[i] = dg + ca * (gl2 + gr2);
-        CP[i] = i < n_u - 1 ? og - ca * gr2 : 0.0;
+        CP[i] = i < n_u - 1 ? og - ca * gr2 : 0.0f;
       } else {
-        SUB[i] = 0.0; INV[i] = 1.0; CP[i] = 0.0;
+        SUB[i] = 0.0f; INV[i] = 1.0f; CP[i] = 0.0f;
       }
     }
     tri_factor(SUB, INV, CP, AL, FF, GG, m_u, lane, rdu);
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       __syncwarp();
       return;
     }
-    R e_prev = 0.0;
+    float e_prev = 0.f;
     for (int sweep = 1;; ++sweep) {
       for (int i = lane; i < n_u; i += kWarp) XZT[i] = interp_z(XZw, i);
       __syncwarp();
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         const int i = ub + r;
         X[i] = i < n_u ? ra[i] + cb * (static_cast<R>(G[i + 1]) * (XZT[i + 1] - XZT[i]) -
                                        static_cast<R>(G[i]) * (XZT[i] - XZT[i - 1]))
-                       : 0.0;
+                       : 0.0f;
       }
       tri_solve(SUB, INV, CP, FF, GG, X, m_u, lane, rdu);
       __syncwarp();
@@ -239,21 +241,21 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       __syncwarp();
       for (int r = 0; r < m_z; ++r) {
         const int i = zb + r;
-        E1Z[i] = i < n_z ? (rz ? rz[i] : 0.0) + cz * spread(FT, i) : 0.0;
+        E1Z[i] = i < n_z ? (rz ? rz[i] : 0.0f) + cz * spread(FT, i) : 0.0f;
       }
       tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
-      R chg = 0.0, mag = 0.0;
+      float chg = 0.f, mag = 0.f;
       for (int r = 0; r < m_z; ++r) {
         const int i = zb + r;
         const R v = E1Z[i];
-        chg = fmax(chg, fabs(v - XZw[i]));
-        mag = fmax(mag, fabs(v));
+        chg = fmaxf(chg, fabsf((v - XZw[i]).hi));
+        mag = fmaxf(mag, fabsf(v.hi));
         XZw[i] = v;
       }
       __syncwarp();
-      chg = warp_max(chg);
-      mag = warp_max(mag);
-      const R e = chg > 0.0 ? chg / mag : 0.0;
+      chg = warp_max_nonneg(chg);
+      mag = warp_max_nonneg(mag);
+      const float e = chg > 0.f ? __fdividef(chg, mag) : 0.f;
       if (adj_converged(e, e_prev, sweep)) break;
       e_prev = e;
     }
@@ -261,15 +263,16 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
 
   // ---- adjoint state at level m_end, warm starts of the longitudinal solves ----
   double* adj = J.adj;
-  for (int i = lane; i < n_u; i += kWarp) { LU[i] = adj[i]; LD[i] = adj[n_u + i]; }
+  // (kept in FP64 between segments)
+  for (int i = lane; i < n_u; i += kWarp) { LU[i] = df_from_double(adj[i]); LD[i] = df_from_double(adj[n_u + i]); }
   for (int i = lane; i < n_z; i += kWarp) {
-    LZ[i] = adj[2 * n_u + i]; LDZ[i] = adj[2 * n_u + n_z + i];
-    NZ[i] = adj[2 * n_u + 2 * n_z + 2 + i]; XZ[i] = adj[2 * n_u + 3 * n_z + 2 + i];
+    LZ[i] = df_from_double(adj[2 * n_u + i]); LDZ[i] = df_from_double(adj[2 * n_u + n_z + i]);
+    NZ[i] = df_from_double(adj[2 * n_u + 2 * n_z + 2 + i]); XZ[i] = df_from_double(adj[2 * n_u + 3 * n_z + 2 + i]);
   }
-  R luh = adj[2 * n_u + 2 * n_z], ldh = adj[2 * n_u + 2 * n_z + 1];
+  R luh = df_from_double(adj[2 * n_u + 2 * n_z]), ldh = df_from_double(adj[2 * n_u + 2 * n_z + 1]);
   R acc[kGradSlots];
 #pragma unroll
-  for (int k = 0; k < kGradSlots; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kGradSlots; ++k) acc[k] = 0.0f;
 
   // level loaders: m_start from the checkpoint, later levels from the replay
   auto level_ptr = [&](int64_t lev, const float*& pu, const float*& pdu, const float*& pz, const float*& pdz,
@@ -291,8 +294,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     if (zout) {
       if (!has_z) return;   // zeta is identically zero
       if (oln - 1 >= 0 && oln - 1 < n_z) {
-        LZ[oln - 1] += c * (1.0 - olw);
-        if (first_level) LDZ[oln - 1] -= c * (1.0 - olw);
+        LZ[oln - 1] += c * (1.0f - olw);
+        if (first_level) LDZ[oln - 1] -= c * (1.0f - olw);
       }
       if (oln >= 0 && oln < n_z) {
         LZ[oln] += c * olw;
@@ -300,8 +303,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       }
     } else {
       if (on - 1 >= 0 && on - 1 < n_u) {
-        LU[on - 1] += c * (1.0 - ow);
-        if (first_level) LD[on - 1] -= c * (1.0 - ow);
+        LU[on - 1] += c * (1.0f - ow);
+        if (first_level) LD[on - 1] -= c * (1.0f - ow);
       }
       if (on >= 0 && on < n_u) {
         LU[on] += c * ow;
@@ -358,27 +361,27 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     for (int i = lane; i <= n_u; i += kWarp) G[i] = U[i] - U[i - 1];
     if (has_z) {
       for (int i = lane; i < n_u; i += kWarp) {
-        ZT[i] = static_cast<float>(interp_z(Z, i));
-        AZT[i] = static_cast<float>(interp_z(AZ, i));
+        ZT[i] = interp_z(Z, i).hi;   // the nearest float
+        AZT[i] = interp_z(AZ, i).hi;
       }
     }
     __syncwarp();
     if (!linear) assemble_u();
-    R eta = 0.0, k2G = 0.0;
+    R eta = 0.0f, k2G = 0.0f;
     if (hammer) {
-      eta = static_cast<R>(uh) - ((1.0 - ew) * static_cast<R>(U[en - 1]) + ew * static_cast<R>(U[en]));
-      if (eta > 0.0) k2G = hk2w * pow(eta, hexpo);
+      eta = static_cast<R>(uh) - ((1.0f - ew) * static_cast<R>(U[en - 1]) + ew * static_cast<R>(U[en]));
+      if (eta > 0.0f) k2G = hk2w * df_from_double(pow(to_double(eta), to_double(hexpo)));   // (FP64: contact only)
     }
     // ---- transposed solve ----
-    const R mus = hammer ? -(ldh + luh) / hM : 0.0;
+    const R mus = hammer ? -(ldh + luh) / hM : 0.0f;
     for (int r = 0; r < m_u; ++r) {
       const int i = ub + r;
-      RA[i] = i < n_u ? LD[i] + LU[i] : 0.0;
+      RA[i] = i < n_u ? LD[i] + LU[i] : 0.0f;
     }
-    const R zs = has_z ? cz / cb : 0.0;
+    const R zs = has_z ? cz / cb : 0.0f;
     for (int r = 0; r < m_z; ++r) {
       const int i = zb + r;
-      RZ_[i] = i < n_z ? zs * (LDZ[i] + LZ[i]) : 0.0;
+      RZ_[i] = i < n_z ? zs * (LDZ[i] + LZ[i]) : 0.0f;
     }
     __syncwarp();
     coupled(RA, RZ_, NA, NZ);
@@ -386,46 +389,46 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     // bow (Eq. 5) with force on: sliding, R3 = s + k^2 F phi(v) with
     // v = I(a + 2D) / 2k - v_B; sticking (v = 0), R3 = v.  Either way M^T
     // adds a rank-one term along the unit-force response.
-    const bool bow_on = bow && n < brel && bF > 0.0;
+    const bool bow_on = bow && n < brel && bF > 0.0f;
     const R vb = uh1;
-    R phid = 0.0;
-    if (bow_on) phid = -ba * (1.0 - beps) * exp(-ba * fabs(vb));
-    if (hammer && k2G > 0.0) {
-      const R rs = -(hM * k2G / (2.0 * js)) * mus;
+    R phid = 0.0f;
+    if (bow_on) phid = -ba * (1.0f - beps) * df_from_double(exp(-to_double(ba) * ::fabs(static_cast<double>(uh1))));
+    if (hammer && k2G > 0.0f) {
+      const R rs = -(hM * k2G / (2.0f * js)) * mus;
       for (int r = 0; r < m_u; ++r) {
         const int i = ub + r;
-        R v = 0.0;
-        if (i == en - 1) v += (1.0 - ew) * js;
+        R v = 0.0f;
+        if (i == en - 1) v += (1.0f - ew) * js;
         if (i == en) v += ew * js;
-        T1[i] = i < n_u ? v : 0.0;
+        T1[i] = i < n_u ? v : 0.0f;
       }
       __syncwarp();
       coupled(T1, nullptr, XP, XZ);
-      const R cm = 0.5 * hM * k2G;
-      const R ia = (1.0 - ew) * NA[en - 1] + ew * NA[en], ix = (1.0 - ew) * XP[en - 1] + ew * XP[en];
-      const R st = (rs - cm * ia) / (1.0 + 0.5 * k2G + cm * ix);
+      const R cm = 0.5f * hM * k2G;
+      const R ia = (1.0f - ew) * NA[en - 1] + ew * NA[en], ix = (1.0f - ew) * XP[en - 1] + ew * XP[en];
+      const R st = (rs - cm * ia) / (1.0f + 0.5f * k2G + cm * ix);
       for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
       for (int i = lane; i < n_z; i += kWarp) NZ[i] = fma(st, XZ[i], NZ[i]);
-      nus = -(2.0 * js / (hM * k2G)) * st;
+      nus = -(2.0f * js / (hM * k2G)) * st;
       __syncwarp();
     } else if (bow_on) {
       for (int r = 0; r < m_u; ++r) {
         const int i = ub + r;
-        R v = 0.0;
-        if (i == en - 1) v += (1.0 - ew) * js;
+        R v = 0.0f;
+        if (i == en - 1) v += (1.0f - ew) * js;
         if (i == en) v += ew * js;
-        T1[i] = i < n_u ? v : 0.0;
+        T1[i] = i < n_u ? v : 0.0f;
       }
       __syncwarp();
       coupled(T1, nullptr, XP, XZ);
-      const R ia = (1.0 - ew) * NA[en - 1] + ew * NA[en], ix = (1.0 - ew) * XP[en - 1] + ew * XP[en];
+      const R ia = (1.0f - ew) * NA[en - 1] + ew * NA[en], ix = (1.0f - ew) * XP[en - 1] + ew * XP[en];
       R st;
-      if (vb == 0.0) {   // sticking: I nu_a = 0
+      if (vb == 0.0f) {   // sticking: I nu_a = 0
         st = -ia / ix;
-        nus = 2.0 * kk * js * st;
+        nus = 2.0f * kk * js * st;
       } else {           // sliding
-        const R bj = 0.5 * kk * bF * phid;
-        st = -bj * ia / (1.0 + bj * ix);
+        const R bj = 0.5f * kk * bF * phid;
+        st = -bj * ia / (1.0f + bj * ix);
         nus = -js * (ia + st * ix);
       }
       for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       __syncwarp();
     }
     // nu_z = (cb / cz) nz; the warm start of the next step keeps nz
-    const R zr = has_z ? cb / cz : 0.0;
+    const R zr = has_z ? cb / cz : 0.0f;
     for (int i = lane; i < n_z; i += kWarp) T2[i] = zr * NZ[i];
     __syncwarp();
     const R* NUZ = T2;
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     // ---- (dR/dx)^T nu and (dR/dc)^T nu ----
     R pg[kGradSlots];
 #pragma unroll
-    for (int k = 0; k < kGradSlots; ++k) pg[k] = 0.0;
+    for (int k = 0; k < kGradSlots; ++k) pg[k] = 0.0f;
     if (has_z) {
       for (int i = lane; i < n_u; i += kWarp) PNZ[i] = interp_z(NUZ, i);
       __syncwarp();
@@ -451,17 +454,17 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     for (int i = lane; i <= n_u; i += kWarp) {
       const R g = G[i], psi = NA[i] - NA[i - 1];
       const R sa = static_cast<R>(A[i]) - A[i - 1];
-      R e = 0.0, q = 0.0, chi = 0.0;
+      R e = 0.0f, q = 0.0f, chi = 0.0f;
       if (has_z) {
         e = static_cast<R>(ZT[i]) - ZT[i - 1];
         q = static_cast<R>(AZT[i]) - AZT[i - 1];
         chi = PNZ[i] - PNZ[i - 1];
       }
-      GAM[i] = -psi * (6.0 * ca * g * g + 4.0 * cb * e + cb * q + 2.0 * ca * g * sa) - chi * (4.0 * cz * g + cz * sa);
+      GAM[i] = -psi * (6.0f * ca * g * g + 4.0f * cb * e + cb * q + 2.0f * ca * g * sa) - chi * (4.0f * cz * g + cz * sa);
       PSG[i] = psi * g;
-      pg[kGCa] -= psi * (2.0 * g * g * g + g * g * sa);
-      pg[kGCb] -= psi * (4.0 * g * e + g * q);
-      pg[kGCz] -= chi * (2.0 * g * g + g * sa);
+      pg[kGCa] -= psi * (2.0f * g * g * g + g * g * sa);
+      pg[kGCb] -= psi * (4.0f * g * e + g * q);
+      pg[kGCz] -= chi * (2.0f * g * g + g * sa);
     }
     __syncwarp();
     for (int i = lane; i < n_u; i += kWarp) {
@@ -470,15 +473,15 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       const R na = NA[i], lu = LU[i];
       R lun = lu + lam2 * d2na - mu2 * d4na;
       if (!linear) lun += GAM[i] - GAM[i + 1];
-      LD[i] = LD[i] + lu - 2.0 * s0u * na + 2.0 * s1 * d2na;
+      LD[i] = LD[i] + lu - 2.0f * s0u * na + 2.0f * s1 * d2na;
       LU[i] = lun;
       pg[kGLam2] += na * d2u;
       // nu . d4 u summed by parts: (d2 nu) . (d2 u) plus the ghost's corner terms
       R nd4u = d2na * d2u;
-      if (i == 0 || i == n_u - 1) nd4u += (1.0 + bsgn) * na * static_cast<R>(U[i]);
+      if (i == 0 || i == n_u - 1) nd4u += (1.0f + bsgn) * na * static_cast<R>(U[i]);
       pg[kGMu2] -= nd4u;
-      pg[kGS0u] += na * (-2.0 * static_cast<R>(DU[i]) - static_cast<R>(A[i]));
-      pg[kGS1] += na * (2.0 * d2du + d2a);
+      pg[kGS0u] += na * (-2.0f * static_cast<R>(DU[i]) - static_cast<R>(A[i]));
+      pg[kGS1] += na * (2.0f * d2du + d2a);
     }
     if (has_z) {
       for (int i = lane; i < n_u; i += kWarp) FT[i] = PSG[i + 1] - PSG[i];   // d_+[psi g] at the rows
@@ -487,23 +490,23 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         const R nz = NUZ[i];
         const R d2n = d2_of(NUZ, i), d2z = d2_of(Z, i), d2dz = d2_of(DZ, i), d2az = d2_of(AZ, i);
         const R lz = LZ[i];
-        LDZ[i] = LDZ[i] + lz - 2.0 * s0 * nz + 2.0 * s1l * d2n;
-        LZ[i] = lz + lam2l * d2n + 4.0 * cb * spread(FT, i);
+        LDZ[i] = LDZ[i] + lz - 2.0f * s0 * nz + 2.0f * s1l * d2n;
+        LZ[i] = lz + lam2l * d2n + 4.0f * cb * spread(FT, i);
         pg[kGLam2l] += nz * d2z;
-        pg[kGS0] += nz * (-2.0 * static_cast<R>(DZ[i]) - static_cast<R>(AZ[i]));
-        pg[kGS1l] += nz * (2.0 * d2dz + d2az);
+        pg[kGS0] += nz * (-2.0f * static_cast<R>(DZ[i]) - static_cast<R>(AZ[i]));
+        pg[kGS1l] += nz * (2.0f * d2dz + d2az);
       }
     }
     __syncwarp();
     if (hammer) {
-      R psi_eta = 0.0;
-      if (k2G > 0.0) {
+      R psi_eta = 0.0f;
+      if (k2G > 0.0f) {
         const R dG = hexpo * k2G / eta;
-        const R ia = (1.0 - ew) * static_cast<R>(A[en - 1]) + ew * static_cast<R>(A[en]);
-        psi_eta = nus * (hM * k2G + (hM * eta - 0.5 * hM * ia - 0.5 * s_h) * dG);
+        const R ia = (1.0f - ew) * static_cast<R>(A[en - 1]) + ew * static_cast<R>(A[en]);
+        psi_eta = nus * (hM * k2G + (hM * eta - 0.5f * hM * ia - 0.5f * s_h) * dG);
       }
-      if (lane == 0 && psi_eta != 0.0) {
-        if (en - 1 >= 0 && en - 1 < n_u) LU[en - 1] -= psi_eta * (1.0 - ew);
+      if (lane == 0 && psi_eta != 0.0f) {
+        if (en - 1 >= 0 && en - 1 < n_u) LU[en - 1] -= psi_eta * (1.0f - ew);
         if (en >= 0 && en < n_u) LU[en] -= psi_eta * ew;
       }
       ldh = ldh + luh;
@@ -511,10 +514,10 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     }
     if (bow_on && lane == 0) {
       // (dR3/dD)^T nu_s and dR3/dv_B (the amplitude slot of a bowed string)
-      const R cd = vb == 0.0 ? 1.0 / kk : kk * bF * phid;
-      if (en - 1 >= 0 && en - 1 < n_u) LD[en - 1] += cd * (1.0 - ew) * nus;
+      const R cd = vb == 0.0f ? 1.0f / kk : kk * bF * phid;
+      if (en - 1 >= 0 && en - 1 < n_u) LD[en - 1] += cd * (1.0f - ew) * nus;
       if (en >= 0 && en < n_u) LD[en] += cd * ew * nus;
-      pg[kGAmp] += vb == 0.0 ? -nus : -kk * kk * bF * phid * nus;
+      pg[kGAmp] += vb == 0.0f ? -nus : -kk * kk * bF * phid * nus;
     }
     __syncwarp();
     if (mod_kind != 0) {   // d(coefficient of step n) / d(unscaled coefficient) = rm
@@ -540,12 +543,12 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     __syncwarp();
     add_output(J.dy[0], true);
     __syncwarp();
-    R pa = 0.0;
+    R pa = 0.0f;
     if (J.pluck_pos >= 0.f) {   // u^0 = u^1 = c0 tri(x), D^1 = 0
       const R xp = J.pluck_pos;
       for (int i = lane; i < n_u; i += kWarp) {
         const R x = static_cast<R>(i + 1) * inv_nt;
-        const R tri = x <= xp ? x / xp : (1.0 - x) / (1.0 - xp);
+        const R tri = x <= xp ? x / xp : (1.0f - x) / (1.0f - xp);
         pa += LU[i] * tri;
       }
     } else if (hammer && lane == 0) {   // u_H^1 = D_H^1 = v k
@@ -555,18 +558,18 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   }
 
   // ---- store the adjoint state, the warm starts and the gradients ----
-  for (int i = lane; i < n_u; i += kWarp) { adj[i] = LU[i]; adj[n_u + i] = LD[i]; }
+  for (int i = lane; i < n_u; i += kWarp) { adj[i] = to_double(LU[i]); adj[n_u + i] = to_double(LD[i]); }
   for (int i = lane; i < n_z; i += kWarp) {
-    adj[2 * n_u + i] = LZ[i]; adj[2 * n_u + n_z + i] = LDZ[i];
-    adj[2 * n_u + 2 * n_z + 2 + i] = NZ[i]; adj[2 * n_u + 3 * n_z + 2 + i] = XZ[i];
+    adj[2 * n_u + i] = to_double(LZ[i]); adj[2 * n_u + n_z + i] = to_double(LDZ[i]);
+    adj[2 * n_u + 2 * n_z + 2 + i] = to_double(NZ[i]); adj[2 * n_u + 3 * n_z + 2 + i] = to_double(XZ[i]);
   }
-  if (lane == 0) { adj[2 * n_u + 2 * n_z] = luh; adj[2 * n_u + 2 * n_z + 1] = ldh; }
+  if (lane == 0) { adj[2 * n_u + 2 * n_z] = to_double(luh); adj[2 * n_u + 2 * n_z + 1] = to_double(ldh); }
 #pragma unroll
   for (int k = 0; k < kGradSlots; ++k) {
     R v = acc[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SFD_FULL, v, o);
-    if (lane == 0) J.grad[k] += v;
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    if (lane == 0) J.grad[k] += to_double(v);
   }
 }
 

@@ -7,11 +7,19 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "sfd_df64.cuh"
 #include "sfd_types.h"
 
 namespace sfd {
 
 #define SFD_FULL 0xffffffffu
+
+// whole-warp shuffles by precision (the templated solvers below; df64 in
+// sfd_df64.cuh)
+__device__ __forceinline__ float shfl_up(float v, int s) { return __shfl_up_sync(SFD_FULL, v, s); }
+__device__ __forceinline__ float shfl_down(float v, int s) { return __shfl_down_sync(SFD_FULL, v, s); }
+__device__ __forceinline__ double shfl_up(double v, int s) { return __shfl_up_sync(SFD_FULL, v, s); }
+__device__ __forceinline__ double shfl_down(double v, int s) { return __shfl_down_sync(SFD_FULL, v, s); }
 
 template <class T>
 struct RedT {          // per-lane factors of the reduced (lane-boundary) system
@@ -42,8 +50,10 @@ constexpr float kPcrDrop = 7.4505806e-9f;   // 2^-27
 // the adjoint sweep)
 __device__ __forceinline__ float rcp_of(float x) { return fast_rcp(x); }
 __device__ __forceinline__ double rcp_of(double x) { return 1.0 / x; }
+__device__ __forceinline__ df64 rcp_of(df64 x) { return rcp_df(x); }
 __device__ __forceinline__ float pcr_drop(float) { return kPcrDrop; }
 __device__ __forceinline__ double pcr_drop(double) { return 8.673617379884035e-19; }   // 2^-60
+__device__ __forceinline__ float pcr_drop(df64) { return 7.105427357601002e-15f; }     // 2^-47
 
 // ----------------------------------------------------------------------------
 // Tridiagonal partition solver on a warp.  Row i: a_i x_{i-1} + b_i x_i +
@@ -87,8 +97,8 @@ __device__ __forceinline__ void tri_factor(const T* __restrict__ SUB, T* __restr
     FF[i] = f;
     GG[i] = g;
   }
-  T f0n = __shfl_down_sync(SFD_FULL, FF[base], 1);
-  T g0n = __shfl_down_sync(SFD_FULL, GG[base], 1);
+  T f0n = shfl_down(FF[base], 1);
+  T g0n = shfl_down(GG[base], 1);
   if (lane == kWarp - 1) { f0n = 0; g0n = 0; }
   const T cl = CP[base + m - 1];
   T A = AL[base + m - 1];
@@ -102,10 +112,10 @@ __device__ __forceinline__ void tri_factor(const T* __restrict__ SUB, T* __restr
   for (int l = 0; l < 5; ++l) {
     if (__all_sync(SFD_FULL, fabs(A) + fabs(C) <= pcr_drop(T(0)) * fabs(B))) { rd.nlev = l; break; }
     const int s = 1 << l;
-    T Am = __shfl_up_sync(SFD_FULL, A, s), Bm = __shfl_up_sync(SFD_FULL, B, s);
-    T Cm = __shfl_up_sync(SFD_FULL, C, s);
-    T Ap = __shfl_down_sync(SFD_FULL, A, s), Bp = __shfl_down_sync(SFD_FULL, B, s);
-    T Cp = __shfl_down_sync(SFD_FULL, C, s);
+    T Am = shfl_up(A, s), Bm = shfl_up(B, s);
+    T Cm = shfl_up(C, s);
+    T Ap = shfl_down(A, s), Bp = shfl_down(B, s);
+    T Cp = shfl_down(C, s);
     if (lane < s) { Am = 0; Bm = 1; Cm = 0; }
     if (lane + s >= kWarp) { Ap = 0; Bp = 1; Cp = 0; }
     const T k1 = A * rcp_of(Bm), k2 = C * rcp_of(Bp);
@@ -140,21 +150,21 @@ __device__ __forceinline__ void tri_solve(const T* __restrict__ SUB, const T* __
     e = E[i] - CP[i] * e;
     E[i] = e;
   }
-  T e0n = __shfl_down_sync(SFD_FULL, E[base], 1);
+  T e0n = shfl_down(E[base], 1);
   if (lane == kWarp - 1) e0n = 0;
   T D = dlast - rd.cl * e0n;
 #pragma unroll
   for (int l = 0; l < 5; ++l) {
     if (l >= rd.nlev) break;      // the factorisation dropped the remaining levels (warp-uniform)
     const int s = 1 << l;
-    T Dm = __shfl_up_sync(SFD_FULL, D, s);
-    T Dp = __shfl_down_sync(SFD_FULL, D, s);
+    T Dm = shfl_up(D, s);
+    T Dp = shfl_down(D, s);
     if (lane < s) Dm = 0;
     if (lane + s >= kWarp) Dp = 0;
     D = D - rd.k1[l] * Dm - rd.k2[l] * Dp;
   }
   const T X = D * rd.binv;
-  T Xp = __shfl_up_sync(SFD_FULL, X, 1);
+  T Xp = shfl_up(X, 1);
   if (lane == 0) Xp = 0;
   for (int r = 0; r < m; ++r) {
     const int i = base + r;

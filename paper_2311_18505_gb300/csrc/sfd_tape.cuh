@@ -45,6 +45,8 @@ struct sfd_tape {
   AdjJob* d_ajobs = nullptr;
   bool forward_done = false;
   float* d_traj_full = nullptr;         // every level of every segment (record-on-forward mode)
+  std::vector<size_t> full_off;         // per string: its first float in d_traj_full
+  size_t full_floats = 0;               // floats of the whole record
 };
 
 namespace {
@@ -67,13 +69,12 @@ void tape_free(sfd_tape* t) {
   delete t;
 }
 
-size_t full_traj_bytes(const sfd_tape* t) {
-  return sizeof(float) * static_cast<size_t>(t->n) * t->n_seg * t->traj_stride;
-}
+size_t full_traj_bytes(const sfd_tape* t) { return sizeof(float) * t->full_floats; }
 
-// segment seg of string i in the whole-trajectory record
+// segment seg of string i in the whole-trajectory record (each string's
+// segments at its own record stride)
 float* full_traj(const sfd_tape* t, int i, int seg) {
-  return t->d_traj_full + (static_cast<size_t>(i) * t->n_seg + seg) * t->traj_stride;
+  return t->d_traj_full + t->full_off[i] + static_cast<size_t>(seg) * t->K * t->rec_stride[i];
 }
 
 char* ckpt_slot(const sfd_tape* t, int i, int c) {
@@ -152,6 +153,10 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
     if (e == cudaSuccess) e = cudaMalloc(&t->d_scratch, sizeof(float) * n * static_cast<size_t>(t->K));
     if (e == cudaSuccess) e = cudaMalloc(&t->d_ajobs, sizeof(AdjJob) * n);
     if (e != cudaSuccess) rc = cuda_fail(e, "tape buffers");
+  }
+  for (int i = 0; rc == SFD_OK && i < n; ++i) {
+    t->full_off.push_back(t->full_floats);
+    t->full_floats += static_cast<size_t>(t->n_seg) * t->K * t->rec_stride[i];
   }
   if (rc == SFD_OK && full_traj_bytes(t) <= kRecordForwardBytes) {
     // record on the forward pass when the device has room; else replay
