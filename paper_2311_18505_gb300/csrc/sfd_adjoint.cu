@@ -27,8 +27,11 @@
 //
 // The states of the segment's levels come from a replay of the forward
 // kernel from a checkpoint (Job::traj), so the adjoint is that of the FP32
-// trajectory the forward produced.  One warp per string, every per-row
-// array in shared memory.
+// trajectory the forward produced.  One block of four warps per string
+// (one per SM sub-partition), every per-row array in shared memory: the row
+// loops are spread over the block's threads, the partitioned tridiagonal
+// solves run on warp 0 (lane partitions and cyclic reduction over its
+// shuffles) between block barriers.
 //
 // The adjoint recursion runs in double-float arithmetic (sfd_df64.cuh,
 // ~48 bits; the trajectory stays FP32): nu carries a large smooth part, and
@@ -55,6 +58,8 @@ namespace {
 using R = df64;
 constexpr float kAdjTol = 1e-13f;   // relative change that ends an adjoint block Gauss-Seidel solve
 constexpr int kAdjSweeps = 40;
+constexpr int kAdjWarps = 4;          // warps per string (one per SM sub-partition)
+constexpr int kAdjThreads = kAdjWarps * kWarp;
 
 // (the change measures e are float: they only decide when to stop)
 __device__ __forceinline__ bool adj_converged(float e, float e_prev, int sweep) {
@@ -66,9 +71,11 @@ __device__ __forceinline__ bool adj_converged(float e, float e_prev, int sweep) 
 
 }  // namespace
 
-__global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict__ jobs, int n_jobs) {
+__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_kernel(const AdjJob* __restrict__ jobs, int n_jobs) {
   extern __shared__ double smem_d[];
-  const int lane = threadIdx.x;
+  __shared__ float red[2][2][kAdjWarps];   // block maxima of the sweep's change measures (two buffers)
+  __shared__ R gsum[kAdjWarps][kGradSlots];   // per-warp gradient sums
+  const int tid = threadIdx.x, lane = tid & (kWarp - 1), warp = tid >> 5;
   if (static_cast<int>(blockIdx.x) >= n_jobs) return;
   const AdjJob J = jobs[blockIdx.x];
   const Desc* __restrict__ Dp = J.desc;
@@ -131,23 +138,22 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   }
   {
     const int nd = static_cast<int>(pd - rbase);
-    for (int k = lane; k < nd; k += kWarp) smem_d[k] = 0.0f;
+    for (int k = tid; k < nd; k += kAdjThreads) smem_d[k] = 0.0f;
     float* f0 = reinterpret_cast<float*>(smem_d + nd);
     const int nf = static_cast<int>(pf - f0);
-    for (int k = lane; k < nf; k += kWarp) f0[k] = 0.f;
+    for (int k = tid; k < nf; k += kAdjThreads) f0[k] = 0.f;
   }
-  __syncwarp();
+  __syncthreads();
 
-  const int ub = lane * m_u, zb = lane * m_z;
   // grid transfer P (longitudinal -> transverse nodes) and P^T, as the forward
   if (has_z) {
-    for (int i = lane; i < n_u; i += kWarp) {
+    for (int i = tid; i < n_u; i += kAdjThreads) {
       const int pos = (i + 1) * n_l;
       const int mm = pos / n_t;
       TMI[i] = mm;
       TMW[i] = static_cast<float>(pos - mm * n_t) / static_cast<float>(n_t);
     }
-    for (int i = lane; i < n_z; i += kWarp) {
+    for (int i = tid; i < n_z; i += kAdjThreads) {
       const int mm = i + 1;
       const int lo = ((mm - 1) * n_t) / n_l + 1;
       const int hi = ((mm + 1) * n_t + n_l - 1) / n_l - 1;
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       ZHI[i] = hi > n_t - 1 ? n_t - 1 : hi;
     }
   }
-  __syncwarp();
+  __syncthreads();
   const R inv_nt = 1.0f / static_cast<R>(n_t);
   auto interp_z = [&](const auto* X, int i) -> R {
     const int mm = TMI[i];
@@ -184,22 +190,54 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     return d4;
   };
 
+  // ---- the partitioned tridiagonal solves: warp 0 (rows lane m .. lane m + m - 1,
+  // cyclic reduction across its lanes), between block barriers; the other
+  // warps take part in the row loops around them ----
+  RedT<R> rdu, rdz;   // (valid in warp 0)
+  auto factor_u = [&]() {
+    __syncthreads();
+    if (warp == 0) tri_factor(SUB, INV, CP, AL, FF, GG, m_u, lane, rdu);
+    __syncthreads();
+  };
+  auto solve_u = [&](R* X) {
+    __syncthreads();
+    if (warp == 0) tri_solve(SUB, INV, CP, FF, GG, X, m_u, lane, rdu);
+    __syncthreads();
+  };
+  auto solve_z = [&](R* X) {
+    __syncthreads();
+    if (warp == 0) tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, X, m_z, lane, rdz);
+    __syncthreads();
+  };
+  // block-wide maxima of two non-negative floats (double-buffered slots)
+  int rbuf = 0;
+  auto block_max2 = [&](float& a, float& b) {
+    a = warp_max_nonneg(a);
+    b = warp_max_nonneg(b);
+    if (lane == 0) { red[rbuf][0][warp] = a; red[rbuf][1][warp] = b; }
+    __syncthreads();
+    a = red[rbuf][0][0];
+    b = red[rbuf][1][0];
+#pragma unroll
+    for (int w = 1; w < kAdjWarps; ++w) { a = fmaxf(a, red[rbuf][0][w]); b = fmaxf(b, red[rbuf][1][w]); }
+    rbuf ^= 1;
+  };
+
   // ---- constant matrices ----
-  RedT<R> rdu, rdz;
   if (has_z) {
     const R dzd = 1.0f + s0 + 2.0f * s1l;
-    for (int r = 0; r < m_z; ++r) {
-      const int i = zb + r;
+    for (int i = tid; i < kWarp * m_z; i += kAdjThreads) {
       const bool real = i < n_z;
       SUBZ[i] = real && i > 0 ? -s1l : 0.0f;
       INVZ[i] = real ? dzd : 1.0f;
       CPZ[i] = real && i < n_z - 1 ? -s1l : 0.0f;
     }
-    tri_factor(SUBZ, INVZ, CPZ, ALZ, FFZ, GGZ, m_z, lane, rdz);
+    __syncthreads();
+    if (warp == 0) tri_factor(SUBZ, INVZ, CPZ, ALZ, FFZ, GGZ, m_z, lane, rdz);
+    __syncthreads();
   }
   auto assemble_u = [&]() {   // A_u(g) at the current level
-    for (int r = 0; r < m_u; ++r) {
-      const int i = ub + r;
+    for (int i = tid; i < kWarp * m_u; i += kAdjThreads) {
       if (i < n_u) {
         const R gl = G[i], gr = G[i + 1];
         const R gl2 = linear ? 0.0f : gl * gl, gr2 = linear ? 0.0f : gr * gr;
@@ -210,51 +248,43 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         SUB[i] = 0.0f; INV[i] = 1.0f; CP[i] = 0.0f;
       }
     }
-    tri_factor(SUB, INV, CP, AL, FF, GG, m_u, lane, rdu);
+    factor_u();
   };
   if (linear) assemble_u();
-  __syncwarp();
+  __syncthreads();
 
   // Solve M (X, XZ) = (ra, rz) (forward form; rz null: zero), block
   // Gauss-Seidel from the warm start in XZw, as the forward kernel.
   auto coupled = [&](const R* ra, const R* rz, R* X, R* XZw) {
     if (!has_z) {
-      for (int r = 0; r < m_u; ++r) X[ub + r] = ra[ub + r];
-      tri_solve(SUB, INV, CP, FF, GG, X, m_u, lane, rdu);
-      __syncwarp();
+      for (int i = tid; i < kWarp * m_u; i += kAdjThreads) X[i] = ra[i];
+      solve_u(X);
       return;
     }
     float e_prev = 0.f;
     for (int sweep = 1;; ++sweep) {
-      for (int i = lane; i < n_u; i += kWarp) XZT[i] = interp_z(XZw, i);
-      __syncwarp();
-      for (int r = 0; r < m_u; ++r) {
-        const int i = ub + r;
+      for (int i = tid; i < n_u; i += kAdjThreads) XZT[i] = interp_z(XZw, i);
+      __syncthreads();
+      for (int i = tid; i < kWarp * m_u; i += kAdjThreads) {
         X[i] = i < n_u ? ra[i] + cb * (static_cast<R>(G[i + 1]) * (XZT[i + 1] - XZT[i]) -
                                        static_cast<R>(G[i]) * (XZT[i] - XZT[i - 1]))
                        : 0.0f;
       }
-      tri_solve(SUB, INV, CP, FF, GG, X, m_u, lane, rdu);
-      __syncwarp();
-      for (int i = lane; i < n_u; i += kWarp)
+      solve_u(X);
+      for (int i = tid; i < n_u; i += kAdjThreads)
         FT[i] = static_cast<R>(G[i + 1]) * (X[i + 1] - X[i]) - static_cast<R>(G[i]) * (X[i] - X[i - 1]);
-      __syncwarp();
-      for (int r = 0; r < m_z; ++r) {
-        const int i = zb + r;
+      __syncthreads();
+      for (int i = tid; i < kWarp * m_z; i += kAdjThreads)
         E1Z[i] = i < n_z ? (rz ? rz[i] : 0.0f) + cz * spread(FT, i) : 0.0f;
-      }
-      tri_solve(SUBZ, INVZ, CPZ, FFZ, GGZ, E1Z, m_z, lane, rdz);
+      solve_z(E1Z);
       float chg = 0.f, mag = 0.f;
-      for (int r = 0; r < m_z; ++r) {
-        const int i = zb + r;
+      for (int i = tid; i < kWarp * m_z; i += kAdjThreads) {
         const R v = E1Z[i];
         chg = fmaxf(chg, fabsf((v - XZw[i]).hi));
         mag = fmaxf(mag, fabsf(v.hi));
         XZw[i] = v;
       }
-      __syncwarp();
-      chg = warp_max_nonneg(chg);
-      mag = warp_max_nonneg(mag);
+      block_max2(chg, mag);   // (its barrier also orders the XZw updates)
       const float e = chg > 0.f ? __fdividef(chg, mag) : 0.f;
       if (adj_converged(e, e_prev, sweep)) break;
       e_prev = e;
@@ -264,8 +294,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   // ---- adjoint state at level m_end, warm starts of the longitudinal solves ----
   double* adj = J.adj;
   // (kept in FP64 between segments)
-  for (int i = lane; i < n_u; i += kWarp) { LU[i] = df_from_double(adj[i]); LD[i] = df_from_double(adj[n_u + i]); }
-  for (int i = lane; i < n_z; i += kWarp) {
+  for (int i = tid; i < n_u; i += kAdjThreads) { LU[i] = df_from_double(adj[i]); LD[i] = df_from_double(adj[n_u + i]); }
+  for (int i = tid; i < n_z; i += kAdjThreads) {
     LZ[i] = df_from_double(adj[2 * n_u + i]); LDZ[i] = df_from_double(adj[2 * n_u + n_z + i]);
     NZ[i] = df_from_double(adj[2 * n_u + 2 * n_z + 2 + i]); XZ[i] = df_from_double(adj[2 * n_u + 3 * n_z + 2 + i]);
   }
@@ -290,7 +320,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   // (LD, LDZ also take -c w for the first sample, which reads level 1 - D)
   auto add_output = [&](R dyv, bool first_level) {
     const R c = dyv * oscale;
-    if (lane != 0) return;
+    if (tid != 0) return;
     if (zout) {
       if (!has_z) return;   // zeta is identically zero
       if (oln - 1 >= 0 && oln - 1 < n_z) {
@@ -319,10 +349,10 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
   {
     const float *pu, *pdu, *pz, *pdz;
     level_ptr(J.m_end, pu, pdu, pz, pdz, uh1, dh1);
-    for (int i = lane; i < n_u; i += kWarp) DN1[i] = pdu[i];
-    for (int i = lane; i < n_z; i += kWarp) DZN1[i] = pdz[i];
+    for (int i = tid; i < n_u; i += kAdjThreads) DN1[i] = pdu[i];
+    for (int i = tid; i < n_z; i += kAdjThreads) DZN1[i] = pdz[i];
   }
-  __syncwarp();
+  __syncthreads();
 
   for (int64_t m = J.m_end; m > J.m_start; --m) {
     const int64_t n = m - 1;
@@ -343,13 +373,13 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     {
       const float *pu, *pdu, *pz, *pdz;
       level_ptr(n, pu, pdu, pz, pdz, uh, dh);
-      for (int i = lane; i < n_u; i += kWarp) {
+      for (int i = tid; i < n_u; i += kAdjThreads) {
         U[i] = pu[i];
         const float d = pdu[i];
         DU[i] = d;
         A[i] = DN1[i] - d;
       }
-      for (int i = lane; i < n_z; i += kWarp) {
+      for (int i = tid; i < n_z; i += kAdjThreads) {
         Z[i] = pz[i];
         const float d = pdz[i];
         DZ[i] = d;
@@ -357,15 +387,15 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       }
     }
     const R s_h = -hM * (static_cast<R>(dh1) - dh);   // hammer force of the step (k^2-scaled)
-    __syncwarp();
-    for (int i = lane; i <= n_u; i += kWarp) G[i] = U[i] - U[i - 1];
+    __syncthreads();
+    for (int i = tid; i <= n_u; i += kAdjThreads) G[i] = U[i] - U[i - 1];
     if (has_z) {
-      for (int i = lane; i < n_u; i += kWarp) {
+      for (int i = tid; i < n_u; i += kAdjThreads) {
         ZT[i] = interp_z(Z, i).hi;   // the nearest float
         AZT[i] = interp_z(AZ, i).hi;
       }
     }
-    __syncwarp();
+    __syncthreads();
     if (!linear) assemble_u();
     R eta = 0.0f, k2G = 0.0f;
     if (hammer) {
@@ -374,16 +404,10 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     }
     // ---- transposed solve ----
     const R mus = hammer ? -(ldh + luh) / hM : 0.0f;
-    for (int r = 0; r < m_u; ++r) {
-      const int i = ub + r;
-      RA[i] = i < n_u ? LD[i] + LU[i] : 0.0f;
-    }
+    for (int i = tid; i < kWarp * m_u; i += kAdjThreads) RA[i] = i < n_u ? LD[i] + LU[i] : 0.0f;
     const R zs = has_z ? cz / cb : 0.0f;
-    for (int r = 0; r < m_z; ++r) {
-      const int i = zb + r;
-      RZ_[i] = i < n_z ? zs * (LDZ[i] + LZ[i]) : 0.0f;
-    }
-    __syncwarp();
+    for (int i = tid; i < kWarp * m_z; i += kAdjThreads) RZ_[i] = i < n_z ? zs * (LDZ[i] + LZ[i]) : 0.0f;
+    __syncthreads();
     coupled(RA, RZ_, NA, NZ);
     R nus = mus;
     // bow (Eq. 5) with force on: sliding, R3 = s + k^2 F phi(v) with
@@ -395,31 +419,30 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     if (bow_on) phid = -ba * (1.0f - beps) * df_from_double(exp(-to_double(ba) * ::fabs(static_cast<double>(uh1))));
     if (hammer && k2G > 0.0f) {
       const R rs = -(hM * k2G / (2.0f * js)) * mus;
-      for (int r = 0; r < m_u; ++r) {
-        const int i = ub + r;
+      for (int i = tid; i < kWarp * m_u; i += kAdjThreads) {
         R v = 0.0f;
         if (i == en - 1) v += (1.0f - ew) * js;
         if (i == en) v += ew * js;
         T1[i] = i < n_u ? v : 0.0f;
       }
-      __syncwarp();
+      __syncthreads();
       coupled(T1, nullptr, XP, XZ);
       const R cm = 0.5f * hM * k2G;
       const R ia = (1.0f - ew) * NA[en - 1] + ew * NA[en], ix = (1.0f - ew) * XP[en - 1] + ew * XP[en];
       const R st = (rs - cm * ia) / (1.0f + 0.5f * k2G + cm * ix);
-      for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
-      for (int i = lane; i < n_z; i += kWarp) NZ[i] = fma(st, XZ[i], NZ[i]);
+      __syncthreads();   // every thread has read NA at the contact point
+      for (int i = tid; i < n_u; i += kAdjThreads) NA[i] = fma(st, XP[i], NA[i]);
+      for (int i = tid; i < n_z; i += kAdjThreads) NZ[i] = fma(st, XZ[i], NZ[i]);
       nus = -(2.0f * js / (hM * k2G)) * st;
-      __syncwarp();
+      __syncthreads();
     } else if (bow_on) {
-      for (int r = 0; r < m_u; ++r) {
-        const int i = ub + r;
+      for (int i = tid; i < kWarp * m_u; i += kAdjThreads) {
         R v = 0.0f;
         if (i == en - 1) v += (1.0f - ew) * js;
         if (i == en) v += ew * js;
         T1[i] = i < n_u ? v : 0.0f;
       }
-      __syncwarp();
+      __syncthreads();
       coupled(T1, nullptr, XP, XZ);
       const R ia = (1.0f - ew) * NA[en - 1] + ew * NA[en], ix = (1.0f - ew) * XP[en - 1] + ew * XP[en];
       R st;
@@ -431,14 +454,15 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         st = -bj * ia / (1.0f + bj * ix);
         nus = -js * (ia + st * ix);
       }
-      for (int i = lane; i < n_u; i += kWarp) NA[i] = fma(st, XP[i], NA[i]);
-      for (int i = lane; i < n_z; i += kWarp) NZ[i] = fma(st, XZ[i], NZ[i]);
-      __syncwarp();
+      __syncthreads();   // every thread has read NA at the bow
+      for (int i = tid; i < n_u; i += kAdjThreads) NA[i] = fma(st, XP[i], NA[i]);
+      for (int i = tid; i < n_z; i += kAdjThreads) NZ[i] = fma(st, XZ[i], NZ[i]);
+      __syncthreads();
     }
     // nu_z = (cb / cz) nz; the warm start of the next step keeps nz
     const R zr = has_z ? cb / cz : 0.0f;
-    for (int i = lane; i < n_z; i += kWarp) T2[i] = zr * NZ[i];
-    __syncwarp();
+    for (int i = tid; i < n_z; i += kAdjThreads) T2[i] = zr * NZ[i];
+    __syncthreads();
     const R* NUZ = T2;
 
     // ---- (dR/dx)^T nu and (dR/dc)^T nu ----
@@ -446,12 +470,12 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
 #pragma unroll
     for (int k = 0; k < kGradSlots; ++k) pg[k] = 0.0f;
     if (has_z) {
-      for (int i = lane; i < n_u; i += kWarp) PNZ[i] = interp_z(NUZ, i);
-      __syncwarp();
+      for (int i = tid; i < n_u; i += kAdjThreads) PNZ[i] = interp_z(NUZ, i);
+      __syncthreads();
     }
     // intervals (for a linear string, alpha = 1, only the c_a term is first
     // order in alpha: the longitudinal field and its adjoint stay zero)
-    for (int i = lane; i <= n_u; i += kWarp) {
+    for (int i = tid; i <= n_u; i += kAdjThreads) {
       const R g = G[i], psi = NA[i] - NA[i - 1];
       const R sa = static_cast<R>(A[i]) - A[i - 1];
       R e = 0.0f, q = 0.0f, chi = 0.0f;
@@ -466,8 +490,8 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       pg[kGCb] -= psi * (4.0f * g * e + g * q);
       pg[kGCz] -= chi * (2.0f * g * g + g * sa);
     }
-    __syncwarp();
-    for (int i = lane; i < n_u; i += kWarp) {
+    __syncthreads();
+    for (int i = tid; i < n_u; i += kAdjThreads) {
       const R d2na = d2_of(NA, i), d4na = d4_of(NA, i);
       const R d2u = d2_of(U, i), d2du = d2_of(DU, i), d2a = d2_of(A, i);
       const R na = NA[i], lu = LU[i];
@@ -484,9 +508,9 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
       pg[kGS1] += na * (2.0f * d2du + d2a);
     }
     if (has_z) {
-      for (int i = lane; i < n_u; i += kWarp) FT[i] = PSG[i + 1] - PSG[i];   // d_+[psi g] at the rows
-      __syncwarp();
-      for (int i = lane; i < n_z; i += kWarp) {
+      for (int i = tid; i < n_u; i += kAdjThreads) FT[i] = PSG[i + 1] - PSG[i];   // d_+[psi g] at the rows
+      __syncthreads();
+      for (int i = tid; i < n_z; i += kAdjThreads) {
         const R nz = NUZ[i];
         const R d2n = d2_of(NUZ, i), d2z = d2_of(Z, i), d2dz = d2_of(DZ, i), d2az = d2_of(AZ, i);
         const R lz = LZ[i];
@@ -497,7 +521,7 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         pg[kGS1l] += nz * (2.0f * d2dz + d2az);
       }
     }
-    __syncwarp();
+    __syncthreads();
     if (hammer) {
       R psi_eta = 0.0f;
       if (k2G > 0.0f) {
@@ -505,21 +529,21 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
         const R ia = (1.0f - ew) * static_cast<R>(A[en - 1]) + ew * static_cast<R>(A[en]);
         psi_eta = nus * (hM * k2G + (hM * eta - 0.5f * hM * ia - 0.5f * s_h) * dG);
       }
-      if (lane == 0 && psi_eta != 0.0f) {
+      if (tid == 0 && psi_eta != 0.0f) {
         if (en - 1 >= 0 && en - 1 < n_u) LU[en - 1] -= psi_eta * (1.0f - ew);
         if (en >= 0 && en < n_u) LU[en] -= psi_eta * ew;
       }
       ldh = ldh + luh;
       luh = luh + psi_eta;
     }
-    if (bow_on && lane == 0) {
+    if (bow_on && tid == 0) {
       // (dR3/dD)^T nu_s and dR3/dv_B (the amplitude slot of a bowed string)
       const R cd = vb == 0.0f ? 1.0f / kk : kk * bF * phid;
       if (en - 1 >= 0 && en - 1 < n_u) LD[en - 1] += cd * (1.0f - ew) * nus;
       if (en >= 0 && en < n_u) LD[en] += cd * ew * nus;
       pg[kGAmp] += vb == 0.0f ? -nus : -kk * kk * bF * phid * nus;
     }
-    __syncwarp();
+    __syncthreads();
     if (mod_kind != 0) {   // d(coefficient of step n) / d(unscaled coefficient) = rm
       pg[kGLam2] *= rmd;
       pg[kGLam2l] *= rmd;
@@ -534,42 +558,49 @@ __global__ void __launch_bounds__(32, 1) adjoint_kernel(const AdjJob* __restrict
     if (has_z) { float* t = DZN1; DZN1 = DZ; DZ = t; }
     dh1 = dh;
     uh1 = uh;
-    __syncwarp();
+    __syncthreads();
   }
 
   if (J.first) {
     // level 1 output, level 0 output y^0 = L I(u^1 - D^1), initial-state terms
     add_output(J.dy[1], false);
-    __syncwarp();
+    __syncthreads();
     add_output(J.dy[0], true);
-    __syncwarp();
+    __syncthreads();
     R pa = 0.0f;
     if (J.pluck_pos >= 0.f) {   // u^0 = u^1 = c0 tri(x), D^1 = 0
       const R xp = J.pluck_pos;
-      for (int i = lane; i < n_u; i += kWarp) {
+      for (int i = tid; i < n_u; i += kAdjThreads) {
         const R x = static_cast<R>(i + 1) * inv_nt;
         const R tri = x <= xp ? x / xp : (1.0f - x) / (1.0f - xp);
         pa += LU[i] * tri;
       }
-    } else if (hammer && lane == 0) {   // u_H^1 = D_H^1 = v k
+    } else if (hammer && tid == 0) {   // u_H^1 = D_H^1 = v k
       pa = static_cast<R>(Dp->k) * (luh + ldh);
     }
     acc[kGAmp] += pa;
   }
 
   // ---- store the adjoint state, the warm starts and the gradients ----
-  for (int i = lane; i < n_u; i += kWarp) { adj[i] = to_double(LU[i]); adj[n_u + i] = to_double(LD[i]); }
-  for (int i = lane; i < n_z; i += kWarp) {
+  for (int i = tid; i < n_u; i += kAdjThreads) { adj[i] = to_double(LU[i]); adj[n_u + i] = to_double(LD[i]); }
+  for (int i = tid; i < n_z; i += kAdjThreads) {
     adj[2 * n_u + i] = to_double(LZ[i]); adj[2 * n_u + n_z + i] = to_double(LDZ[i]);
     adj[2 * n_u + 2 * n_z + 2 + i] = to_double(NZ[i]); adj[2 * n_u + 3 * n_z + 2 + i] = to_double(XZ[i]);
   }
-  if (lane == 0) { adj[2 * n_u + 2 * n_z] = to_double(luh); adj[2 * n_u + 2 * n_z + 1] = to_double(ldh); }
+  if (tid == 0) { adj[2 * n_u + 2 * n_z] = to_double(luh); adj[2 * n_u + 2 * n_z + 1] = to_double(ldh); }
 #pragma unroll
   for (int k = 0; k < kGradSlots; ++k) {
     R v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
-    if (lane == 0) J.grad[k] += to_double(v);
+    if (lane == 0) gsum[warp][k] = v;
+  }
+  __syncthreads();
+  if (tid < kGradSlots) {
+    R v = gsum[0][tid];
+#pragma unroll
+    for (int w = 1; w < kAdjWarps; ++w) v += gsum[w][tid];
+    J.grad[tid] += to_double(v);
   }
 }
 
@@ -601,11 +632,20 @@ cudaError_t raise_adjoint_smem_limit() {
 }
 }  // namespace
 
-// Host-side launcher (called by sfd_api.cu): one warp per job.
+// Static shared memory of the adjoint kernel (its reduction cells), which a
+// launch's dynamic shared memory must leave room for.
+cudaError_t adjoint_static_smem(size_t* bytes) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, adjoint_kernel);
+  if (e == cudaSuccess) *bytes = fa.sharedSizeBytes;
+  return e;
+}
+
+// Host-side launcher (called by sfd_api.cu): one block of kAdjWarps warps per job.
 cudaError_t launch_adjoint(const AdjJob* d_jobs, int n_jobs, int smem_bytes, cudaStream_t stream) {
   cudaError_t e = raise_adjoint_smem_limit();
   if (e != cudaSuccess) return e;
-  adjoint_kernel<<<n_jobs, kWarp, static_cast<size_t>(smem_bytes), stream>>>(d_jobs, n_jobs);
+  adjoint_kernel<<<n_jobs, kAdjThreads, static_cast<size_t>(smem_bytes), stream>>>(d_jobs, n_jobs);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 
 namespace sfd {
 cudaError_t launch_adjoint(const AdjJob* d_jobs, int n_jobs, int smem_bytes, cudaStream_t stream);
+cudaError_t adjoint_static_smem(size_t* bytes);
 }
 
 namespace {
@@ -143,7 +144,12 @@ sfd_status sfd_tape_create(sfd_ctx* c, int32_t n, const sfd_string_params* param
     t->adj_stride = std::max(t->adj_stride, round_up(2 * D.n_u + 4 * D.n_z + 2, 64));
     t->adj_smem = std::max(t->adj_smem, adj_smem_bytes(D.m_u, D.m_z));
   }
-  if (rc == SFD_OK && static_cast<size_t>(t->adj_smem) > c->smem_optin)
+  size_t adj_static = 0;
+  if (rc == SFD_OK) {
+    const cudaError_t e = adjoint_static_smem(&adj_static);
+    if (e != cudaSuccess) rc = cuda_fail(e, "adjoint kernel attributes");
+  }
+  if (rc == SFD_OK && static_cast<size_t>(t->adj_smem) + adj_static > c->smem_optin)
     rc = fail(SFD_EINVAL, "a string's grid exceeds the adjoint kernel's shared memory");
   if (rc == SFD_OK) {
     cudaError_t e = cudaMalloc(&t->d_ckpt, static_cast<size_t>(n) * (t->n_seg + 1) * t->ckpt_stride);
