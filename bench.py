@@ -671,7 +671,8 @@ WORKLOAD_GRADIENT = ("differentiation: 64 plucked or hammered strings x 0.5 s at
 
 def run_gradient(args, ws, rank, local):
     """Time forward synthesis plus the reverse sweep of the discrete adjoint
-    (segment replay from checkpoints + adjoint kernel) on the
+    (the forward records the trajectory when it fits, else each segment is
+    replayed from its checkpoint; then the adjoint kernel) on the
     differentiation workload."""
     import torch
     from paper_2311_18505_gb300 import build as B
@@ -729,7 +730,7 @@ def run_gradient(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": ws * samples / t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (forward), f64 (adjoint recursion)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 (forward), double-float f32x2 (adjoint recursion)", "data": "synthetic",
         "config": {"workload": WORKLOAD_GRADIENT, "strings": len(base), "samples_per_string": n,
                    "checkpoint_every": 1024, "timing": "host wall clock around the two C-ABI calls (each "
                    "synchronises its stream)"},
