@@ -34,6 +34,14 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# A batch's kernel classes run concurrently, one stream each.  With the CUDA
+# runtime's default of 8 hardware work queues, steps enqueued back to back
+# (as the timed loop does) put two class kernels of a step behind one queue
+# some of the time: measured on the 4096-string batch, 4.53-5.46 s per step
+# with the default against 4.51-4.78 s with 32 queues (4.52 s with a
+# synchronisation after every step).  The setting must precede CUDA's
+# initialisation; a value the caller set is kept.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -413,6 +421,8 @@ def run_ours(args, ws, rank, local):
     clk = clocks.stop()
     sfd.sfd_ctx_set_timing(ctx, False)
     times_ms = [a.elapsed_time(b) for a, b in ev]
+    if rank == 0:
+        print("step ms:", " ".join(f"{t:.1f}" for t in times_ms), file=sys.stderr)
     y = out[: min(total, 1 << 20)].float().cpu().numpy()
     finite = bool(np.all(np.isfinite(y)))
     for hb, g in batches:
