@@ -36,11 +36,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 # A batch's kernel classes run concurrently, one stream each.  With the CUDA
 # runtime's default of 8 hardware work queues, steps enqueued back to back
-# (as the timed loop does) put two class kernels of a step behind one queue
-# some of the time: measured on the 4096-string batch, 4.53-5.46 s per step
-# with the default against 4.51-4.78 s with 32 queues (4.52 s with a
-# synchronisation after every step).  The setting must precede CUDA's
-# initialisation; a value the caller set is kept.
+# (--enqueue-ahead) put two class kernels of a step behind one queue some of
+# the time: measured on the 4096-string batch, a mean of 4.96 s per step with
+# the default against 4.81 s with 32 queues (4.52 s with each step launched
+# once the previous one ended, the timed loop's default).  The setting must
+# precede CUDA's initialisation; a value the caller set is kept.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -411,6 +411,12 @@ def run_ours(args, ws, rank, local):
         ev[i][0].record(stream)
         run_step(hb, g)
         ev[i][1].record(stream)
+        if not args.enqueue_ahead:
+            # launched on an idle GPU, the class kernels start in launch order,
+            # heaviest first; enqueued behind a running step they become ready
+            # together and the GPU's dispatch order varies (4.5-5.5 s per
+            # step on the 4096-string batch against 4.51-4.55 s this way)
+            ev[i][1].synchronize()
         launches += len(set(classes)) if g is not None else sfd.sfd_last_launch_count(ctx)
         if g is None:
             # per-class kernel times, recorded with events on each kernel's own stream
@@ -544,7 +550,10 @@ def run_ours(args, ws, rank, local):
                    "samples_per_step": total, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": ("one CUDA-graph replay per step (concurrent class kernels), warps per CTA "
                               f"{'set' if args.warps_per_cta else 'autotuned'} to {wpc}") if graphed else
-                             "one persistent kernel per class per step, one warp per string"},
+                             "one persistent kernel per class per step, one warp per string",
+                   "step_issue": ("enqueued back to back" if args.enqueue_ahead else
+                                  "each timed step launched once the previous one ended (host waits on its "
+                                  "end event; the value sums the steps' event times)")},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "fp32_frac": achieved / peak,
                      "frac_minimal_counts": achieved_min / peak,
@@ -917,6 +926,8 @@ def parse_args(argv=None):
     ap.add_argument("--strings", type=int, default=0)
     ap.add_argument("--seconds", type=float, default=0.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--enqueue-ahead", action="store_true",
+                    help="launch each timed step without waiting for the previous one to end")
     ap.add_argument("--warp-groups", type=int, default=1, choices=[0, 1],
                     help="1: large-grid strings may take 2 or 4 warps (sfd_ctx_set_warp_pairs)")
     ap.add_argument("--e2e-steps", type=int, default=3)

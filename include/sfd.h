@@ -316,7 +316,12 @@ sfd_status sfd_batch_autotune(sfd_batch* b, int64_t probe_samples, int32_t* best
  * allocation), so it may be captured into a CUDA graph and replayed: every
  * launch or replay advances each string by its n_samples and overwrites the
  * same output ranges.  Per-class kernel timing is skipped while the
- * context stream is capturing. */
+ * context stream is capturing.  The kernel classes run concurrently,
+ * launched heaviest first; on an idle device they start in that order, but
+ * enqueued behind a running batch they become ready together and the
+ * device may start a light class first, which can lengthen the batch by up
+ * to ~20 %: for the best schedule, launch (or replay) after the previous
+ * batch has ended. */
 sfd_status sfd_batch_prepare(sfd_batch* b, const int64_t* n_samples, float* out_device, const int64_t* out_offsets);
 sfd_status sfd_batch_launch(sfd_batch* b);
 
