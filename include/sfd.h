@@ -249,7 +249,12 @@ sfd_status sfd_batch_create(sfd_ctx* ctx, int32_t n, sfd_string* const* strings,
 sfd_status sfd_batch_synthesize(sfd_batch* b, const int64_t* n_samples, float* out_device,
                                 const int64_t* out_offsets, int32_t* per_string_status);
 
-/* Same, with host output: copies the samples to out_host after the launch. */
+/* Same, with host output, and returns once out_host holds every string's
+ * samples (out_host + out_offsets[i], n_samples[i] floats each; elements
+ * between the strings' ranges are not written).  The kernel classes run
+ * concurrently, and each class's strings are copied as soon as its kernel
+ * ends, while the other classes still run; pinned out_host lets those
+ * copies overlap the kernels. */
 sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, float* out_host,
                                      const int64_t* out_offsets, int32_t* per_string_status);
 

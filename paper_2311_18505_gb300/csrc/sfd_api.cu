@@ -132,6 +132,8 @@ struct sfd_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side[kClasses] = {};      // one per kernel class, forked from `stream`
   cudaEvent_t fork = nullptr, join[kClasses] = {};
+  cudaStream_t copy = nullptr;           // host-output copies of classes already ended
+  cudaEvent_t copied = nullptr;          // end of those copies, joined back to `stream`
   bool timing = false;                   // record per-class kernel times
   cudaEvent_t t0[kClasses] = {}, t1[kClasses] = {};
   int timed_jobs[kClasses] = {};         // jobs of each class in the last launch
@@ -207,9 +209,9 @@ cudaError_t h2d(sfd_ctx* c, void* dst, const void* src, size_t n) {
   return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream);
 }
 
-cudaError_t d2h(sfd_ctx* c, void* dst, const void* src, size_t n) {
+cudaError_t d2h(sfd_ctx* c, void* dst, const void* src, size_t n, cudaStream_t st = nullptr) {
   c->d2h_bytes += n;
-  return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream);
+  return cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, st ? st : c->stream);
 }
 
 // Transverse and longitudinal grids from the spacing rules (Sec. 3.2).
@@ -871,7 +873,7 @@ sfd_status issue_plan(sfd_ctx* c, const Plan& P, const Job* d_jobs) {
 // Queue the persistent kernels for `jobs` on the context stream (job table
 // uploaded into the context's table).
 sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<const sfd_string*>& owners,
-                       int wpc_override = 0, int groups_override = -1) {
+                       int wpc_override = 0, int groups_override = -1, Plan* keep = nullptr) {
   c->last_launches = 0;
   if (jobs.empty()) return SFD_OK;
   Plan P;
@@ -880,7 +882,35 @@ sfd_status launch_jobs(sfd_ctx* c, std::vector<Job>& jobs, const std::vector<con
   rc = ensure_jobs(c, static_cast<int>(P.jobs.size()));
   if (rc) return rc;
   SFD_CUDA(h2d(c, c->d_jobs, P.jobs.data(), sizeof(Job) * P.jobs.size()));
-  return issue_plan(c, P, c->d_jobs);
+  rc = issue_plan(c, P, c->d_jobs);
+  if (keep) *keep = std::move(P);
+  return rc;
+}
+
+// Copy every job's output from the device to out_host (the same offsets
+// from dout), each class's jobs on the context's copy stream as soon as
+// that class's kernel has ended (its join event), so that only the last
+// class's copies follow the launch's end; the context stream then waits for
+// them.  A plan with one class, whose kernel ran on the context stream,
+// copies after it there.
+sfd_status copy_out_by_class(sfd_ctx* c, const Plan& P, const float* dout, float* out_host) {
+  int active = 0;
+  for (int k = 0; k < kClasses; ++k) active += P.first[k + 1] > P.first[k];
+  const cudaStream_t st = active > 1 ? c->copy : c->stream;
+  for (int kk = 0; kk < kClasses; ++kk) {
+    const int k = P.order[kk];
+    if (P.first[k + 1] == P.first[k]) continue;
+    if (active > 1) SFD_CUDA(cudaStreamWaitEvent(st, c->join[k], 0));
+    for (int j = P.first[k]; j < P.first[k + 1]; ++j) {
+      const Job& J = P.jobs[j];
+      SFD_CUDA(d2h(c, out_host + (J.out - dout), J.out, sizeof(float) * static_cast<size_t>(J.n_samples), st));
+    }
+  }
+  if (active > 1) {
+    SFD_CUDA(cudaEventRecord(c->copied, st));
+    SFD_CUDA(cudaStreamWaitEvent(c->stream, c->copied, 0));
+  }
+  return SFD_OK;
 }
 
 sfd_status read_status(const sfd_string* s, Scalars* out) {
@@ -991,7 +1021,9 @@ sfd_status sfd_ctx_create(int device, void* cuda_stream, size_t mem_budget_bytes
     delete c;
     return cuda_fail(e, "cudaMalloc(counter)");
   }
-  bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess;
+  bool ok = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < kClasses && ok; ++k) {
     ok = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) == cudaSuccess &&
@@ -1016,6 +1048,8 @@ void sfd_ctx_destroy(sfd_ctx* c) {
     if (c->t1[k]) cudaEventDestroy(c->t1[k]);
   }
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->copy) cudaStreamDestroy(c->copy);
+  if (c->copied) cudaEventDestroy(c->copied);
   if (c->stage_done) cudaEventDestroy(c->stage_done);
   if (c->stage) cudaFreeHost(c->stage);
   c->pool.release();
@@ -1569,7 +1603,7 @@ sfd_status sfd_batch_create(sfd_ctx* c, int32_t n, sfd_string* const* strings, s
 }
 
 static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_device, const int64_t* offsets,
-                            int32_t* per_string_status) {
+                            int32_t* per_string_status, Plan* keep = nullptr) {
   sfd_ctx* c = b->ctx;
   sfd_status rc = set_device(c);
   if (rc) return rc;
@@ -1582,7 +1616,7 @@ static sfd_status batch_run(sfd_batch* b, const int64_t* n_samples, float* out_d
     jobs.push_back(Job{b->strings[i]->d_desc, out_device + offsets[i], n_samples[i]});
     owners.push_back(b->strings[i]);
   }
-  rc = launch_jobs(c, jobs, owners, b->wpc, b->groups);
+  rc = launch_jobs(c, jobs, owners, b->wpc, b->groups, keep);
   for (auto* s : b->strings) s->started = true;
   if (rc) return rc;
   if (per_string_status) {
@@ -1612,11 +1646,15 @@ sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, flo
   char* tmp = c->pool.alloc(sizeof(float) * std::max<int64_t>(total, 1));
   if (!tmp) return fail(SFD_ENOMEM, "device pool exhausted for the output buffer");
   float* dout = reinterpret_cast<float*>(tmp);
-  rc = batch_run(b, n_samples, dout, out_offsets, nullptr);
+  Plan P;
+  rc = batch_run(b, n_samples, dout, out_offsets, nullptr, &P);
   if (rc == SFD_OK) {
-    cudaError_t e = d2h(c, out_host, dout, sizeof(float) * total);
-    if (e != cudaSuccess) rc = cuda_fail(e, "copy out");
-    e = cudaStreamSynchronize(c->stream);
+    rc = copy_out_by_class(c, P, dout, out_host);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    // the copy stream too: after a failed copy call the context stream was
+    // not made to wait for the copies already queued there
+    const cudaError_t e2 = cudaStreamSynchronize(c->copy);
+    if (e == cudaSuccess) e = e2;
     if (rc == SFD_OK && e != cudaSuccess) rc = cuda_fail(e, "sync");
   }
   if (rc == SFD_OK && per_string_status) {

@@ -293,3 +293,48 @@ def test_modulation_grows_the_grid_before_the_first_synthesis(sfd):
         sfd.sfd_string_destroy(s)
     finally:
         sfd.sfd_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_output_copies_each_class_and_nothing_else(sfd, pinned):
+    """sfd_batch_synthesize_host copies each class's strings as its kernel
+    ends: every string's range equals the device-output launch bit for bit,
+    in any offset order, with gaps between ranges and strings of zero
+    samples left unwritten, into pinned or pageable host memory."""
+    ctx = sfd.sfd_ctx_create(0, None, 256 << 20)
+    try:
+        strings = W.batch_modulated(24, seconds=0.02, seed=47)
+        ns = np.array([d["n_samples"] for d in strings], np.int64)
+        ns[5] = 0
+        order = np.arange(len(ns))[::-1]            # offsets in reverse string order, 37-sample gaps
+        offs = np.zeros(len(ns), np.int64)
+        pos = 11
+        for i in order:
+            offs[i] = pos
+            pos += int(ns[i]) + 37
+        total = pos
+        hs, b = make_batch(sfd, ctx, strings)
+        classes = {sfd.sfd_string_kernel_class(h) for h in hs}
+        dev = torch.full((total,), 7.0, dtype=torch.float32, device="cuda")
+        sfd.sfd_batch_synthesize(b, ns, dev, offs)
+        torch.cuda.synchronize()
+        ref = dev.cpu().numpy()
+        free(sfd, hs, b)
+        hs, b = make_batch(sfd, ctx, strings)
+        host = torch.full((total,), 7.0, dtype=torch.float32)
+        if pinned:
+            host = host.pin_memory()
+        rc = sfd.lib().sfd_batch_synthesize_host(
+            b, ns.ctypes.data_as(sfd.ctypes.POINTER(sfd.ctypes.c_int64)), host.data_ptr(),
+            offs.ctypes.data_as(sfd.ctypes.POINTER(sfd.ctypes.c_int64)), None)
+        free(sfd, hs, b)
+        assert rc == sfd.SFD_OK, sfd.sfd_last_error()
+        got = host.numpy()
+        assert len(classes) >= 2
+        written = np.zeros(total, bool)
+        for o, n in zip(offs, ns):
+            written[o:o + n] = True
+        assert np.array_equal(got[written], ref[written])
+        assert np.all(got[~written] == 7.0)
+    finally:
+        sfd.sfd_ctx_destroy(ctx)
