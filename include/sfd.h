@@ -251,10 +251,12 @@ sfd_status sfd_batch_synthesize(sfd_batch* b, const int64_t* n_samples, float* o
 
 /* Same, with host output, and returns once out_host holds every string's
  * samples (out_host + out_offsets[i], n_samples[i] floats each; elements
- * between the strings' ranges are not written).  The kernel classes run
- * concurrently, and each class's strings are copied as soon as its kernel
- * ends, while the other classes still run; pinned out_host lets those
- * copies overlap the kernels. */
+ * between the strings' ranges are not written).  Pinned host memory that
+ * the ctx's device can address (cudaHostAlloc, cudaHostRegister, a pinned
+ * torch tensor) is written by the kernels directly, with no copy after
+ * them.  Other host memory receives device-side output copied class by
+ * class: the kernel classes run concurrently, and each class's strings are
+ * copied as soon as its kernel ends, while the other classes still run. */
 sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, float* out_host,
                                      const int64_t* out_offsets, int32_t* per_string_status);
 
@@ -297,8 +299,9 @@ sfd_status sfd_ctx_set_sweep_cap(sfd_ctx* ctx, int32_t cap);
 /* Kernel class (0 .. SFD_KERNEL_CLASSES-1) a string runs in. */
 sfd_status sfd_string_kernel_class(const sfd_string* s, int32_t* cls);
 
-/* Cumulative bytes the library copied host->device and device->host on this
- * context (state uploads, job tables, outputs, status reads). */
+/* Cumulative bytes the library moved host->device and device->host on this
+ * context (state uploads, job tables, outputs, status reads; outputs the
+ * kernels wrote straight into pinned host memory count as device->host). */
 sfd_status sfd_ctx_transfer_bytes(const sfd_ctx* ctx, uint64_t* h2d_total, uint64_t* d2h_total);
 
 /* Warps per CTA for this batch's launches: 1..4, or 0 (default) for
