@@ -455,7 +455,8 @@ def run_ours(args, ws, rank, local):
     ms_step = 1e3 * t_total / args.steps
 
     # e2e through the public API with host buffers (create -> synthesize to
-    # pinned host memory -> destroy), wall-clock per step
+    # pinned host memory, which the kernels write directly -> destroy),
+    # wall-clock per step
     e2e = None
     if not args.no_e2e:
         host_out = torch.empty(total, dtype=torch.float32).pin_memory()
