@@ -266,6 +266,13 @@ sfd_status sfd_server_pump(sfd_server* sv, const sfd_chunk** chunks, int32_t* n_
     SFD_CUDA(cudaMemcpyAsync(sv->d_jobs[b], sv->h_jobs[b].p, sizeof(Job) * P.jobs.size(), cudaMemcpyHostToDevice,
                              c->stream));
     c->h2d_bytes += sizeof(Job) * P.jobs.size();
+    // launched on an idle device the classes start in launch order, heaviest
+    // first; enqueued behind the previous chunk they would become ready
+    // together and start in no fixed order (measured on a 20 s trace at
+    // 2000 notes/s: 151.9 and 151.8 M delivered samples/s this way against
+    // 150.3 M, alternating runs).  The host's admission and job-table work
+    // for this chunk has already overlapped the previous one.
+    if (sv->fl[q].active) SFD_CUDA(cudaEventSynchronize(sv->done[q]));
     if ((rc = issue_plan(c, P, reinterpret_cast<const Job*>(sv->d_jobs[b])))) return rc;
     const size_t ob = sizeof(float) * ch.entries.size() * sv->chunk;
     SFD_CUDA(cudaMemcpyAsync(sv->h_out[b].p, dout, ob, cudaMemcpyDeviceToHost, c->stream));
