@@ -390,10 +390,12 @@ sfd_status sfd_synthesize_noalloc(int device, void* cuda_stream, const sfd_strin
  *      later ones wait behind it);
  *   2. enqueues the next chunk (chunk_samples, fewer at a note's end) of
  *      every live note as one persistent launch per kernel class, and the
- *      copy of the chunk's audio to pinned host memory;
- *   3. waits for the chunk enqueued by the previous pump and returns its
- *      audio, one sfd_chunk per live note (so a pump's host work overlaps
- *      the next chunk's GPU work);
+ *      copy of the chunk's audio to pinned host memory; the kernels are
+ *      launched once the previous pump's chunk has ended, so that they
+ *      start in launch order on an idle device;
+ *   3. returns the audio of the chunk enqueued by the previous pump, one
+ *      sfd_chunk per live note (so a pump's host work overlaps the GPU's
+ *      work on a chunk);
  *   4. frees the slots and blocks of the notes that ended in that chunk.
  * A note's audio is bitwise the audio of the same string synthesized alone
  * (chunking and batching do not change a string's arithmetic).  Not

@@ -3,11 +3,13 @@
 // Included once, at the end of sfd_api.cu: it uses that file's internal
 // pieces (pool, string setup, block image, launch plan).
 //
-// Every pump enqueues chunk p (ping-pong buffer p & 1) before it waits for
-// chunk p - 1, so the host's admission and delivery work overlaps the GPU's
-// work on the next chunk.  All host<->device copies go through pinned
-// buffers, so nothing in a pump waits for the stream except the one event
-// of the chunk being delivered.  Buffer p & 1 (output, job table, staging
+// Every pump prepares chunk p (ping-pong buffer p & 1: admission, uploads,
+// job table) while chunk p - 1 runs, waits for chunk p - 1, then launches
+// chunk p's kernels on the idle device and delivers chunk p - 1, so the
+// host's admission and delivery work overlaps the GPU's work and the class
+// kernels start in launch order.  All host<->device copies go through
+// pinned buffers, so nothing in a pump waits for the stream except the one
+// event of the previous chunk.  Buffer p & 1 (output, job table, staging
 // of admitted notes' initial blocks, status scalars) is written again two
 // pumps later, after chunk p has been waited for.
 
