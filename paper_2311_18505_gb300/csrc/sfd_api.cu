@@ -1635,6 +1635,19 @@ sfd_status sfd_batch_synthesize(sfd_batch* b, const int64_t* n_samples, float* o
   return batch_run(b, n_samples, out_device, out_offsets, per_string_status);
 }
 
+// The current device's address of host memory [p, p + n floats) when it is
+// pinned and mapped for this device, with both ends at the same offset;
+// nullptr otherwise (pageable memory, device memory, an unknown pointer).
+static float* device_view(float* p, int64_t n) {
+  cudaPointerAttributes a{}, z{};
+  const bool mapped = cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+                      a.devicePointer && (n <= 1 ||
+                      (cudaPointerGetAttributes(&z, p + (n - 1)) == cudaSuccess && z.type == cudaMemoryTypeHost &&
+                       z.devicePointer == static_cast<void*>(static_cast<float*>(a.devicePointer) + (n - 1))));
+  cudaGetLastError();   // a pointer the runtime does not know is not an error here
+  return mapped ? static_cast<float*>(a.devicePointer) : nullptr;
+}
+
 sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, float* out_host,
                                      const int64_t* out_offsets, int32_t* per_string_status) {
   if (!b || !n_samples || !out_offsets || !out_host) return fail(SFD_EINVAL, "NULL argument");
@@ -1643,28 +1656,30 @@ sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, flo
   for (size_t i = 0; i < b->strings.size(); ++i) total = std::max(total, out_offsets[i] + n_samples[i]);
   sfd_status rc = set_device(c);
   if (rc) return rc;
+  auto statuses = [&]() -> sfd_status {
+    if (!per_string_status) return SFD_OK;
+    for (size_t i = 0; i < b->strings.size(); ++i) {
+      Scalars sc{};
+      if (sfd_status r = read_status(b->strings[i], &sc)) return r;
+      per_string_status[i] = status_code(sc);
+    }
+    return SFD_OK;
+  };
   // Pinned host memory that this device can address: the kernels write the
   // samples there themselves (each warp stores 32 consecutive samples at a
   // time, about 0.7 GB/s for the whole 4096-string batch), so no copy
-  // follows the launch.
-  cudaPointerAttributes pa{};
-  if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
-    rc = batch_run(b, n_samples, static_cast<float*>(pa.devicePointer), out_offsets, nullptr);
+  // follows the launch.  Both ends of the range must map to the device at
+  // the same offset (one allocation, as a C array is).
+  if (float* dv = device_view(out_host, total)) {
+    rc = batch_run(b, n_samples, dv, out_offsets, nullptr);
     if (rc == SFD_OK) {   // device-to-host bytes, moved by the kernels' stores
       for (size_t i = 0; i < b->strings.size(); ++i) c->d2h_bytes += sizeof(float) * static_cast<uint64_t>(n_samples[i]);
     }
     const cudaError_t e = cudaStreamSynchronize(c->stream);
     if (rc == SFD_OK && e != cudaSuccess) rc = cuda_fail(e, "sync");
-    if (rc == SFD_OK && per_string_status) {
-      for (size_t i = 0; i < b->strings.size(); ++i) {
-        Scalars sc{};
-        if ((rc = read_status(b->strings[i], &sc))) break;
-        per_string_status[i] = status_code(sc);
-      }
-    }
+    if (rc == SFD_OK) rc = statuses();
     return rc;
   }
-  cudaGetLastError();   // an unrecognised pointer is not an error here
   char* tmp = c->pool.alloc(sizeof(float) * std::max<int64_t>(total, 1));
   if (!tmp) return fail(SFD_ENOMEM, "device pool exhausted for the output buffer");
   float* dout = reinterpret_cast<float*>(tmp);
@@ -1679,13 +1694,7 @@ sfd_status sfd_batch_synthesize_host(sfd_batch* b, const int64_t* n_samples, flo
     if (e == cudaSuccess) e = e2;
     if (rc == SFD_OK && e != cudaSuccess) rc = cuda_fail(e, "sync");
   }
-  if (rc == SFD_OK && per_string_status) {
-    for (size_t i = 0; i < b->strings.size(); ++i) {
-      Scalars sc{};
-      if ((rc = read_status(b->strings[i], &sc))) break;
-      per_string_status[i] = status_code(sc);
-    }
-  }
+  if (rc == SFD_OK) rc = statuses();
   c->pool.dealloc(tmp);
   return rc;
 }
